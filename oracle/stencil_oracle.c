@@ -1,0 +1,342 @@
+/*
+ * Oracle for the 3D 7-point Jacobi and lexicographic Gauss-Seidel smoothers.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  The product path
+ * (the CUDA library and its Python binding) never calls it and shares no
+ * code, header, table or constant with it.
+ *
+ * Everything here is the plain serial definition, written out loop by loop:
+ *
+ *  - Jacobi (Sec. 3, first listing): out of place, two arrays, every site
+ *        dst = a*src + b*(W + E + S + N + B + T)
+ *    with the neighbour sum taken left to right in the listing's order
+ *    (i-1, i+1, j-1, j+1, k-1, k+1).  For a Poisson right-hand side
+ *    (Sec. 3 names "the Jacobi method for a Poisson problem") the reading is
+ *    -Lap_h u = f, so the bracket becomes (sum + h*h*f).  With a == 0 the
+ *    a*src term is dropped.
+ *  - Gauss-Seidel (Sec. 3, second listing): in place, k outermost, then j,
+ *    then i, all ascending; at the moment of an update the i-1, j-1, k-1
+ *    neighbours already hold this sweep's values.
+ *  - Residual r = f - A u with A u = (6 u - sum) / h^2, and its 2-norm
+ *    (not in the paper; compensated summation so the oracle's norm is
+ *    correct to rounding).
+ *  - Defect correction with single-precision inner sweeps (not in the
+ *    paper): r in double, e solves A e = r by FP32 sweeps from e = 0,
+ *    u += e in double.
+ *
+ * Storage: (nz+2)(ny+2)(nx+2) elements, C order u[k][j][i], i fastest, with a
+ * one-cell Dirichlet halo that is read, never written.  Halo edges and
+ * corners are never read.
+ *
+ * Build with -O2 -ffp-contract=off -fno-fast-math: every + and * below is
+ * one IEEE-754 operation rounded to nearest, never fused.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_OOM (-2)
+#define ORC_NOT_CONVERGED (-5)
+
+typedef struct {
+  int64_t nx, ny, nz; /* interior extents */
+  int64_t sx, sy;     /* strides of j and k in elements: sx = nx+2, sy = (nx+2)(ny+2) */
+} orc_grid;
+
+static int orc_grid_make(orc_grid* g, int64_t nx, int64_t ny, int64_t nz) {
+  if (nx < 0 || ny < 0 || nz < 0) return ORC_ERR_ARG;
+  g->nx = nx; g->ny = ny; g->nz = nz;
+  g->sx = nx + 2;
+  g->sy = (nx + 2) * (ny + 2);
+  return ORC_OK;
+}
+
+static size_t orc_total(const orc_grid* g) { return (size_t)g->sy * (size_t)(g->nz + 2); }
+
+/* index of interior site (i,j,k), 0-based interior coordinates */
+static size_t orc_at(const orc_grid* g, int64_t i, int64_t j, int64_t k) {
+  return (size_t)((k + 1) * g->sy + (j + 1) * g->sx + (i + 1));
+}
+
+/* ---------------------------------------------------------------------------
+ * Double precision
+ * ------------------------------------------------------------------------- */
+
+/* Neighbour sum in the listing's order, left to right. */
+static double orc_sum_d(const double* u, size_t c, int64_t sx, int64_t sy) {
+  double s = u[c - 1] + u[c + 1];
+  s = s + u[c - sx];
+  s = s + u[c + sx];
+  s = s + u[c - sy];
+  s = s + u[c + sy];
+  return s;
+}
+
+/* One site of the smoother: a*u + b*(sum + hh*f). */
+static double orc_site_d(const double* src, const double* f, size_t c, int64_t sx, int64_t sy,
+                         double a, double b, double hh) {
+  double t = orc_sum_d(src, c, sx, sy);
+  if (f) t = t + hh * f[c];
+  double v = b * t;
+  if (a != 0.0) v = a * src[c] + v;
+  return v;
+}
+
+/* Jacobi, Sec. 3 first listing: nsweeps out-of-place sweeps, result in u. */
+int oracle_jacobi_f64(double* u, const double* f, int64_t nx, int64_t ny, int64_t nz, double h,
+                      double a, double b, int nsweeps) {
+  orc_grid g;
+  if (!u || nsweeps < 0 || orc_grid_make(&g, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  if (nsweeps == 0 || nx == 0 || ny == 0 || nz == 0) return ORC_OK;
+  size_t n = orc_total(&g);
+  double* tmp = (double*)malloc(n * sizeof(double));
+  if (!tmp) return ORC_ERR_OOM;
+  memcpy(tmp, u, n * sizeof(double)); /* the second array carries the same halo */
+  const double hh = h * h;
+  double* src = u;
+  double* dst = tmp;
+  for (int it = 0; it < nsweeps; ++it) {
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+          size_t c = orc_at(&g, i, j, k);
+          dst[c] = orc_site_d(src, f, c, g.sx, g.sy, a, b, hh);
+        }
+    double* sw = src; src = dst; dst = sw;
+  }
+  if (src != u) memcpy(u, src, n * sizeof(double));
+  free(tmp);
+  return ORC_OK;
+}
+
+/* Gauss-Seidel, Sec. 3 second listing: in place, lexicographic. */
+int oracle_gs_lex_f64(double* u, const double* f, int64_t nx, int64_t ny, int64_t nz, double h,
+                      double b, int nsweeps) {
+  orc_grid g;
+  if (!u || nsweeps < 0 || orc_grid_make(&g, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  const double hh = h * h;
+  for (int it = 0; it < nsweeps; ++it)
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+          size_t c = orc_at(&g, i, j, k);
+          u[c] = orc_site_d(u, f, c, g.sx, g.sy, 0.0, b, hh);
+        }
+  return ORC_OK;
+}
+
+/* Red-black Gauss-Seidel (Sec. 3 names it as the usual parallel
+ * alternative): all sites with (i+j+k) even, then all with (i+j+k) odd, each
+ * colour in lexicographic order, in place.  Interior coordinates 0-based. */
+int oracle_gs_rb_f64(double* u, const double* f, int64_t nx, int64_t ny, int64_t nz, double h,
+                     double b, int nsweeps) {
+  orc_grid g;
+  if (!u || nsweeps < 0 || orc_grid_make(&g, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  const double hh = h * h;
+  for (int it = 0; it < nsweeps; ++it)
+    for (int colour = 0; colour < 2; ++colour)
+      for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+          for (int64_t i = 0; i < nx; ++i) {
+            if (((i + j + k) & 1) != colour) continue;
+            size_t c = orc_at(&g, i, j, k);
+            u[c] = orc_site_d(u, f, c, g.sx, g.sy, 0.0, b, hh);
+          }
+  return ORC_OK;
+}
+
+/* Neumaier-compensated accumulation of x into (s, c). */
+static void orc_acc(double* s, double* c, double x) {
+  double t = *s + x;
+  if (fabs(*s) >= fabs(x))
+    *c += (*s - t) + x;
+  else
+    *c += (x - t) + *s;
+  *s = t;
+}
+
+/* Residual r = f - A u, A u = (6 u - sum) * (1/h^2), f == NULL meaning f = 0.
+ * r (optional) receives the residual on the interior (halo untouched).
+ * out_norm receives ||r||_2 over the interior; out_fnorm (optional) ||f||_2. */
+int oracle_residual_f64(const double* u, const double* f, int64_t nx, int64_t ny, int64_t nz,
+                        double h, double* r, double* out_norm, double* out_fnorm) {
+  orc_grid g;
+  if (!u || !out_norm || orc_grid_make(&g, nx, ny, nz) != ORC_OK || !(h > 0.0)) return ORC_ERR_ARG;
+  const double ih2 = 1.0 / (h * h);
+  double s = 0.0, cs = 0.0, fs = 0.0, fc = 0.0;
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        size_t c = orc_at(&g, i, j, k);
+        double au = (6.0 * u[c] - orc_sum_d(u, c, g.sx, g.sy)) * ih2;
+        double fv = f ? f[c] : 0.0;
+        double rv = fv - au;
+        if (r) r[c] = rv;
+        orc_acc(&s, &cs, rv * rv);
+        orc_acc(&fs, &fc, fv * fv);
+      }
+  *out_norm = sqrt(s + cs);
+  if (out_fnorm) *out_fnorm = sqrt(fs + fc);
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Single precision: the same definitions with every operation in float.
+ * hh = (float)(h*h), b given as the float constant.
+ * ------------------------------------------------------------------------- */
+
+static float orc_sum_s(const float* u, size_t c, int64_t sx, int64_t sy) {
+  float s = u[c - 1] + u[c + 1];
+  s = s + u[c - sx];
+  s = s + u[c + sx];
+  s = s + u[c - sy];
+  s = s + u[c + sy];
+  return s;
+}
+
+static float orc_site_s(const float* src, const float* f, size_t c, int64_t sx, int64_t sy,
+                        float a, float b, float hh) {
+  float t = orc_sum_s(src, c, sx, sy);
+  if (f) t = t + hh * f[c];
+  float v = b * t;
+  if (a != 0.0f) v = a * src[c] + v;
+  return v;
+}
+
+int oracle_jacobi_f32(float* u, const float* f, int64_t nx, int64_t ny, int64_t nz, double h,
+                      float a, float b, int nsweeps) {
+  orc_grid g;
+  if (!u || nsweeps < 0 || orc_grid_make(&g, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  if (nsweeps == 0 || nx == 0 || ny == 0 || nz == 0) return ORC_OK;
+  size_t n = orc_total(&g);
+  float* tmp = (float*)malloc(n * sizeof(float));
+  if (!tmp) return ORC_ERR_OOM;
+  memcpy(tmp, u, n * sizeof(float));
+  const float hh = (float)(h * h);
+  float* src = u;
+  float* dst = tmp;
+  for (int it = 0; it < nsweeps; ++it) {
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+          size_t c = orc_at(&g, i, j, k);
+          dst[c] = orc_site_s(src, f, c, g.sx, g.sy, a, b, hh);
+        }
+    float* sw = src; src = dst; dst = sw;
+  }
+  if (src != u) memcpy(u, src, n * sizeof(float));
+  free(tmp);
+  return ORC_OK;
+}
+
+int oracle_gs_lex_f32(float* u, const float* f, int64_t nx, int64_t ny, int64_t nz, double h,
+                      float b, int nsweeps) {
+  orc_grid g;
+  if (!u || nsweeps < 0 || orc_grid_make(&g, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  const float hh = (float)(h * h);
+  for (int it = 0; it < nsweeps; ++it)
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+          size_t c = orc_at(&g, i, j, k);
+          u[c] = orc_site_s(u, f, c, g.sx, g.sy, 0.0f, b, hh);
+        }
+  return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * Defect correction with FP32 inner sweeps.
+ *
+ *   r  = f - A u                         (double, oracle_residual_f64)
+ *   rel = ||r|| / ||f||  (||r0|| if f == 0)
+ *   while rel > rtol and outer < max_outer:
+ *       r32 = (float) r                  (interior; halo of e and r32 zero)
+ *       e32 = 0
+ *       inner_sweeps FP32 sweeps of the chosen smoother on A e = r32
+ *       u  += (double) e32               (interior)
+ *       r = f - A u ; rel = ...
+ *
+ * smoother: 0 = Jacobi (a = 0), 1 = lexicographic Gauss-Seidel.
+ * Returns ORC_OK when rel <= rtol, ORC_NOT_CONVERGED otherwise; out_rel and
+ * out_iters are filled either way.
+ * ------------------------------------------------------------------------- */
+int oracle_solve_mixed(double* u, const double* f, int64_t nx, int64_t ny, int64_t nz, double h,
+                       int smoother, double rtol, int max_outer, int inner_sweeps,
+                       double* out_rel, int* out_iters) {
+  orc_grid g;
+  if (!u || orc_grid_make(&g, nx, ny, nz) != ORC_OK || !(h > 0.0) || max_outer < 0 ||
+      inner_sweeps < 0 || (smoother != 0 && smoother != 1))
+    return ORC_ERR_ARG;
+  size_t n = orc_total(&g);
+  double* r = (double*)calloc(n, sizeof(double));
+  float* r32 = (float*)calloc(n, sizeof(float));
+  float* e32 = (float*)calloc(n, sizeof(float));
+  if (!r || !r32 || !e32) { free(r); free(r32); free(e32); return ORC_ERR_OOM; }
+  const float b32 = (float)(1.0 / 6.0);
+  double rn = 0.0, fn = 0.0;
+  oracle_residual_f64(u, f, nx, ny, nz, h, r, &rn, &fn);
+  const double denom = fn > 0.0 ? fn : rn;
+  double rel = denom > 0.0 ? rn / denom : 0.0;
+  int it = 0;
+  while (rel > rtol && it < max_outer) {
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+          size_t c = orc_at(&g, i, j, k);
+          r32[c] = (float)r[c];
+          e32[c] = 0.0f;
+        }
+    if (smoother == 0)
+      oracle_jacobi_f32(e32, r32, nx, ny, nz, h, 0.0f, b32, inner_sweeps);
+    else
+      oracle_gs_lex_f32(e32, r32, nx, ny, nz, h, b32, inner_sweeps);
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+          size_t c = orc_at(&g, i, j, k);
+          u[c] = u[c] + (double)e32[c];
+        }
+    ++it;
+    oracle_residual_f64(u, f, nx, ny, nz, h, r, &rn, NULL);
+    rel = denom > 0.0 ? rn / denom : 0.0;
+  }
+  free(r); free(r32); free(e32);
+  if (out_rel) *out_rel = rel;
+  if (out_iters) *out_iters = it;
+  return rel <= rtol ? ORC_OK : ORC_NOT_CONVERGED;
+}
+
+/* Double-precision-only solve for comparison: plain FP64 sweeps of the
+ * chosen smoother, the residual checked every check_every sweeps, until
+ * rel <= rtol or max_sweeps.  out_sweeps receives the sweeps done. */
+int oracle_solve_f64(double* u, const double* f, int64_t nx, int64_t ny, int64_t nz, double h,
+                     int smoother, double rtol, int max_sweeps, int check_every,
+                     double* out_rel, int* out_sweeps) {
+  orc_grid g;
+  if (!u || orc_grid_make(&g, nx, ny, nz) != ORC_OK || !(h > 0.0) || max_sweeps < 0 ||
+      check_every <= 0 || (smoother != 0 && smoother != 1))
+    return ORC_ERR_ARG;
+  const double b = 1.0 / 6.0;
+  double rn = 0.0, fn = 0.0;
+  oracle_residual_f64(u, f, nx, ny, nz, h, NULL, &rn, &fn);
+  const double denom = fn > 0.0 ? fn : rn;
+  double rel = denom > 0.0 ? rn / denom : 0.0;
+  int done = 0;
+  while (rel > rtol && done < max_sweeps) {
+    int step = check_every < max_sweeps - done ? check_every : max_sweeps - done;
+    if (smoother == 0)
+      oracle_jacobi_f64(u, f, nx, ny, nz, h, 0.0, b, step);
+    else
+      oracle_gs_lex_f64(u, f, nx, ny, nz, h, b, step);
+    done += step;
+    oracle_residual_f64(u, f, nx, ny, nz, h, NULL, &rn, NULL);
+    rel = denom > 0.0 ? rn / denom : 0.0;
+  }
+  if (out_rel) *out_rel = rel;
+  if (out_sweeps) *out_sweeps = done;
+  return rel <= rtol ? ORC_OK : ORC_NOT_CONVERGED;
+}

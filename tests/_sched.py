@@ -1,0 +1,207 @@
+"""Parallel schedules restated on the CPU (test helpers, numpy).
+
+Each function reorders the same site updates as the plain serial loops and
+must reproduce them bit for bit: that is the paper's claim for the pipelined /
+wavefront Gauss-Seidel ("retains the same algorithm as a sequential
+Gauss-Seidel", Sec. 3 and Sec. 5) and for temporal blocking ("no additional
+computations", Sec. 4).  The site formula is the canonical one,
+b*(((((W+E)+S)+N)+B)+T + h*h*f), evaluated with numpy elementwise IEEE
+operations; arrays are padded (nz+2, ny+2, nx+2).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+def _update(src: np.ndarray, f, k, j, i, b, hh):
+    """Vectorised site update at interior coordinates (arrays k, j, i, 0-based),
+    reading neighbours from ``src``; returns the new values (not stored)."""
+    K, J, I = k + 1, j + 1, i + 1
+    s = src[K, J, I - 1] + src[K, J, I + 1]
+    s = s + src[K, J - 1, I]
+    s = s + src[K, J + 1, I]
+    s = s + src[K - 1, J, I]
+    s = s + src[K + 1, J, I]
+    if f is not None:
+        s = s + hh * f[K, J, I]
+    return b * s
+
+
+def _consts(u, h):
+    if u.dtype == np.float32:
+        return np.float32(1.0 / 6.0), np.float32(h * h)
+    return np.float64(1.0 / 6.0), np.float64(h * h)
+
+
+def gs_brute_force(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int = 1) -> np.ndarray:
+    """Pure-Python Gauss-Seidel: sites visited by explicitly sorting all (k, j, i)
+    tuples; Python floats are IEEE binary64.  Tiny grids only."""
+    nz, ny, nx = (s - 2 for s in u.shape)
+    w = {idx: float(v) for idx, v in np.ndenumerate(u)}
+    fv = None if f is None else {idx: float(v) for idx, v in np.ndenumerate(f)}
+    b, hh = 1.0 / 6.0, h * h
+    order = sorted(itertools.product(range(nz), range(ny), range(nx)))
+    for _ in range(nsweeps):
+        for (k, j, i) in order:
+            K, J, I = k + 1, j + 1, i + 1
+            s = w[(K, J, I - 1)] + w[(K, J, I + 1)]
+            s = s + w[(K, J - 1, I)]
+            s = s + w[(K, J + 1, I)]
+            s = s + w[(K - 1, J, I)]
+            s = s + w[(K + 1, J, I)]
+            if fv is not None:
+                s = s + hh * fv[(K, J, I)]
+            w[(K, J, I)] = b * s
+    out = np.empty_like(u)
+    for idx in w:
+        out[idx] = w[idx]
+    return out
+
+
+def gs_hyperplane(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int = 1) -> np.ndarray:
+    """Gauss-Seidel by levels L = i + j + k + 2t: every site of sweep t lies on
+    level i+j+k+2t; all sites of one level are independent and are updated
+    together (read all, then write all)."""
+    u = u.copy()
+    nz, ny, nx = (s - 2 for s in u.shape)
+    b, hh = _consts(u, h)
+    if nsweeps == 0 or nx * ny * nz == 0:
+        return u
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    d = (ii + jj + kk).ravel()
+    ks, js, is_ = kk.ravel(), jj.ravel(), ii.ravel()
+    dmax = nx + ny + nz - 3
+    for L in range(dmax + 2 * (nsweeps - 1) + 1):
+        sel = []
+        for t in range(nsweeps):
+            dd = L - 2 * t
+            if 0 <= dd <= dmax:
+                sel.append(np.nonzero(d == dd)[0])
+        if not sel:
+            continue
+        m = np.concatenate(sel)
+        v = _update(u, f, ks[m], js[m], is_[m], b, hh)
+        u[ks[m] + 1, js[m] + 1, is_[m] + 1] = v
+    return u
+
+
+def pass_stride(nt: int) -> int:
+    return 2 if nt == 1 else 4
+
+
+def skewed_tile_tasks(nx, ny, nz, tile, nt, nsweeps):
+    """Tasks (I, J, K, p) of the skewed-tile schedule, sorted by level
+    I + J + K + c*p.  Pass p covers sweeps [p*nt, min((p+1)*nt, nsweeps)); at the
+    pass-local sweep s the tile covers x in [I*W - s, (I+1)*W - s) (same in y, z).
+
+    c = 2 without skew (nt = 1): a task waits for its three backward face
+    neighbours of the same pass and its three forward face neighbours of the
+    previous pass.  With skew (nt > 1) the previous pass's tiles
+    (I+a, J+b, K+c), a, b, c in {0, 1}, all end inside this task's box, the
+    corner one three levels up, so passes are 4 levels apart."""
+    W, H, D = tile
+    ni = -(-(nx + nt - 1) // W)
+    nj = -(-(ny + nt - 1) // H)
+    nk = -(-(nz + nt - 1) // D)
+    npass = -(-nsweeps // nt)
+    tasks = [(I, J, K, p) for p in range(npass) for K in range(nk) for J in range(nj) for I in range(ni)]
+    c = pass_stride(nt)
+    tasks.sort(key=lambda t: (t[0] + t[1] + t[2] + c * t[3]))
+    return tasks, (ni, nj, nk, npass)
+
+
+def gs_skewed_tiles(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int = 1, tile=(4, 4, 4),
+                    nt: int = 1, reverse_within_level: bool = False) -> np.ndarray:
+    """Gauss-Seidel by skewed tiles (levels I+J+K+c*p, see skewed_tile_tasks).
+
+    A task owns, for each of its pass's sweeps s, the tile shifted by -s in x,
+    y and z.  Tasks run in level order (ties in any order); inside a task the
+    sites go by local level ii + jj + kk - s (ii, jj, kk the tile-local
+    coordinates at sweep s), all sites of a local level together.  The global
+    array is updated in place and doubles as the boundary store between tasks."""
+    u = u.copy()
+    nz, ny, nx = (s - 2 for s in u.shape)
+    b, hh = _consts(u, h)
+    if nsweeps == 0 or nx * ny * nz == 0:
+        return u
+    W, H, D = tile
+    tasks, _ = skewed_tile_tasks(nx, ny, nz, tile, nt, nsweeps)
+    if reverse_within_level:
+        # same level order, reversed order among tasks of one level
+        levels = {}
+        for t in tasks:
+            levels.setdefault(t[0] + t[1] + t[2] + pass_stride(nt) * t[3], []).append(t)
+        tasks = [t for L in sorted(levels) for t in reversed(levels[L])]
+    jj_, ii_ = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    jj_, ii_ = jj_.ravel(), ii_.ravel()
+    for (I, J, K, p) in tasks:
+        ns = min(nt, nsweeps - p * nt)
+        X0, Y0, Z0 = I * W, J * H, K * D
+        for lvl in range(-(ns - 1), W + H + D - 2):
+            ks, js, is_ = [], [], []
+            for s in range(ns):
+                kk = lvl - ii_ - jj_ + s
+                x = X0 - s + ii_
+                y = Y0 - s + jj_
+                z = Z0 - s + kk
+                ok = (kk >= 0) & (kk < D) & (x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0) & (z < nz)
+                ks.append(z[ok]); js.append(y[ok]); is_.append(x[ok])
+            k = np.concatenate(ks); j = np.concatenate(js); i = np.concatenate(is_)
+            if k.size == 0:
+                continue
+            v = _update(u, f, k, j, i, b, hh)
+            u[k + 1, j + 1, i + 1] = v
+    return u
+
+
+def jacobi_wavefront_paper(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int = 2, nt: int = 2) -> np.ndarray:
+    """Jacobi by the Sec. 4 wavefront: one thread group of nt threads over the
+    whole domain.  Thread s (1..nt) performs update s on z-plane p at step
+    p + 2(s-1) (a distance of two between successive updates).  Odd updates
+    write to a small temporary ring (4 planes per odd update, used round
+    robin); even updates write back into ``src`` itself, so no second grid is
+    needed.  nt must be even and divide nsweeps."""
+    assert nt % 2 == 0 and nsweeps % nt == 0
+    src = u.copy()
+    nz, ny, nx = (s - 2 for s in u.shape)
+    b, hh = _consts(u, h)
+    R = 4
+    ring = {s: np.zeros((R, ny + 2, nx + 2), dtype=u.dtype) for s in range(1, nt + 1, 2)}
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+
+    def plane(level, z):
+        """Padded plane z (padded index) of time level ``level`` as currently stored."""
+        if z == 0 or z == nz + 1 or level % 2 == 0:
+            return src[z]
+        return ring[level][z % R]
+
+    for _ in range(nsweeps // nt):
+        # odd-level rings carry the Dirichlet halo of their planes
+        for s in ring:
+            for r in range(R):
+                ring[s][r] = 0
+        for n in range(nz + 2 * (nt - 1)):
+            for s in range(1, nt + 1):
+                p = n - 2 * (s - 1)          # interior plane index being updated
+                if not (0 <= p < nz):
+                    continue
+                z = p + 1                     # padded index
+                lo, mid, hi = plane(s - 1, z - 1), plane(s - 1, z), plane(s - 1, z + 1)
+                J, I = jj + 1, ii + 1
+                acc = mid[J, I - 1] + mid[J, I + 1]
+                acc = acc + mid[J - 1, I]
+                acc = acc + mid[J + 1, I]
+                acc = acc + lo[J, I]
+                acc = acc + hi[J, I]
+                if f is not None:
+                    acc = acc + hh * f[z, J, I]
+                val = b * acc
+                if s % 2 == 1:
+                    dst = ring[s][z % R]
+                    dst[...] = src[z]         # halo ring of the plane
+                    dst[J, I] = val
+                else:
+                    src[z, J, I] = val
+    return src

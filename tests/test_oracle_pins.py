@@ -1,0 +1,313 @@
+"""Pins for the CPU oracle (no GPU): closed forms, textbook routines, brute force
+and invariants, each chosen so a plausible mistake in the oracle (a dropped
+term, a wrong sign or index, a transposed operand, old/new neighbours swapped,
+another summation order) fails at least one of them."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle
+from tests import _forms as F
+from tests import _sched as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS = np.finfo(np.float64).eps
+EPS32 = float(np.finfo(np.float32).eps)
+
+# non-cubic so that a transposed stride or extent cannot pass
+DIMS = [(7, 5, 6), (9, 4, 3), (5, 5, 5)]
+MODES = [(1, 1, 1), (2, 1, 3), (3, 4, 2), (1, 3, 1)]
+
+
+# ---------------------------------------------------------------- Jacobi ----
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("mode", MODES)
+def test_jacobi_sine_mode_decays_by_analytic_factor(dims, mode):
+    """Sec. 3 Jacobi, f = 0, zero Dirichlet: a discrete sine mode is an
+    eigenvector; one sweep multiplies it by mu = (cos a + cos b + cos c)/3."""
+    nx, ny, nz = dims
+    p, q, r = mode
+    if p > nx or q > ny or r > nz:
+        pytest.skip("mode beyond grid")
+    u = F.sine_mode(nx, ny, nz, p, q, r)
+    mu = F.jacobi_factor(nx, ny, nz, p, q, r)
+    for sweeps in (1, 3):
+        out = oracle.jacobi(u, None, 1.0, sweeps)
+        np.testing.assert_allclose(out, (mu ** sweeps) * u, rtol=0, atol=12 * sweeps * EPS)
+
+
+def test_jacobi_weighted_mode_factor():
+    """Weighted form a*u + b*sum (Sec. 3 listing): factor a + 6 b mu."""
+    nx, ny, nz = 7, 5, 6
+    u = F.sine_mode(nx, ny, nz, 2, 1, 3)
+    mu = F.jacobi_factor(nx, ny, nz, 2, 1, 3)
+    a, b = 1.0 - 0.8, 0.8 / 6.0
+    out = oracle.jacobi(u, None, 1.0, 1, a=a, b=b)
+    np.testing.assert_allclose(out, (a + 6 * b * mu) * u, rtol=0, atol=16 * EPS)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_jacobi_matches_sparse_operator(dims):
+    """u' = b (N u + boundary + h^2 f), N the sparse neighbour-sum matrix."""
+    nx, ny, nz = dims
+    rng = np.random.default_rng(11)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    h = 0.37
+    out = oracle.jacobi(u, f, h, 1)
+    ref = (F.neighbour_matrix(nx, ny, nz) @ F.interior(u) + F.boundary_sum(u) + h * h * F.interior(f)) / 6.0
+    np.testing.assert_allclose(F.interior(out), ref, rtol=8 * EPS, atol=8 * EPS)
+    # the halo is never written
+    mask = np.ones(u.shape, bool)
+    mask[1:-1, 1:-1, 1:-1] = False
+    assert np.array_equal(out[mask], u[mask])
+
+
+def test_jacobi_two_sweeps_is_operator_squared():
+    """Out of place: sweep 2 reads only sweep-1 values (matrix form applied twice)."""
+    nx, ny, nz = 6, 5, 4
+    rng = np.random.default_rng(3)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    n = F.neighbour_matrix(nx, ny, nz)
+    bnd = F.boundary_sum(u)
+    x = F.interior(u)
+    for _ in range(2):
+        x = (n @ x + bnd) / 6.0
+    np.testing.assert_allclose(F.interior(oracle.jacobi(u, None, 1.0, 2)), x, rtol=16 * EPS)
+
+
+# ----------------------------------------------------------- Gauss-Seidel ----
+@pytest.mark.parametrize("dims", DIMS)
+def test_gs_is_lower_triangular_solve(dims):
+    """Lexicographic GS (Sec. 3 second listing) is forward substitution:
+    (6 I - L) u_new = U u_old + boundary + h^2 f, L / U the neighbours before /
+    after a site in (k, j, i) order."""
+    nx, ny, nz = dims
+    rng = np.random.default_rng(5)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    h = 0.29
+    L, U = F.lex_split(nx, ny, nz)
+    m = (6.0 * sp.identity(nx * ny * nz) - L).tocsr()
+    rhs = U @ F.interior(u) + F.boundary_sum(u) + h * h * F.interior(f)
+    ref = spla.spsolve_triangular(m, rhs, lower=True)
+    out = oracle.gs_lex(u, f, h, 1)
+    np.testing.assert_allclose(F.interior(out), ref, rtol=64 * EPS, atol=64 * EPS)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4), (1, 1, 6), (6, 1, 1), (3, 5, 7), (1, 1, 1)])
+def test_gs_equals_brute_force_sorted_enumeration(dims):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(7)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    for ff in (None, f):
+        out = oracle.gs_lex(u, ff, 0.5, 3)
+        ref = S.gs_brute_force(u, ff, 0.5, 3)
+        assert np.array_equal(out, ref)
+
+
+def test_gs_red_black_half_sweeps():
+    """Red-black GS: each colour is a simultaneous (Jacobi) update of that
+    colour from the current values, red ((i+j+k) even) first."""
+    nx, ny, nz = 5, 4, 3
+    rng = np.random.default_rng(9)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    n = F.neighbour_matrix(nx, ny, nz)
+    bnd = F.boundary_sum(u)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    red = ((i + j + k) % 2 == 0).ravel()
+    x = F.interior(u)
+    for colour in (red, ~red):
+        y = (n @ x + bnd) / 6.0
+        x = np.where(colour, y, x)
+    np.testing.assert_allclose(F.interior(oracle.gs_rb(u, None, 1.0, 1)), x, rtol=16 * EPS)
+
+
+# ------------------------------------------------- schedules (exactness) ----
+@pytest.mark.parametrize("dims", [(4, 4, 4), (5, 3, 6), (1, 1, 5), (6, 2, 1)])
+def test_gs_hyperplane_order_is_bit_exact(dims):
+    """Sites with equal i+j+k+2t are independent: updating them level by level
+    reproduces the serial sweeps exactly (the pipeline-parallel claim, Sec. 3)."""
+    nx, ny, nz = dims
+    u, f = (np.random.default_rng(1).random((nz + 2, ny + 2, nx + 2)),
+            np.random.default_rng(2).standard_normal((nz + 2, ny + 2, nx + 2)))
+    assert np.array_equal(S.gs_hyperplane(u, f, 0.3, 4), oracle.gs_lex(u, f, 0.3, 4))
+
+
+@pytest.mark.parametrize("tile,nt", [((4, 4, 4), 1), ((3, 2, 4), 1), ((4, 4, 4), 2), ((4, 3, 5), 3),
+                                     ((8, 4, 2), 2), ((2, 2, 2), 2), ((5, 5, 5), 4)])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_gs_skewed_tiles_are_bit_exact(tile, nt, reverse):
+    """The skewed-tile schedule (nt sweeps per task, tasks by level I+J+K+c*p)
+    reproduces the serial sweeps exactly, whatever the order within a level."""
+    nx, ny, nz = 9, 7, 8
+    rng = np.random.default_rng(4)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    for nsweeps in (1, nt, 2 * nt + 1):
+        ref = oracle.gs_lex(u, f, 0.2, nsweeps)
+        out = S.gs_skewed_tiles(u, f, 0.2, nsweeps, tile, nt, reverse)
+        assert np.array_equal(out, ref), (tile, nt, nsweeps)
+
+
+@pytest.mark.parametrize("nt", [2, 4, 6])
+def test_jacobi_paper_wavefront_is_bit_exact(nt):
+    """Sec. 4 wavefront: nt updates per pass, distance two, odd updates in a
+    4-plane ring per update, even updates in place: equals nt plain sweeps
+    (no additional computations, no second grid)."""
+    nx, ny, nz = 7, 6, 9
+    rng = np.random.default_rng(8)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    for ff in (None, f):
+        out = S.jacobi_wavefront_paper(u, ff, 0.25, 2 * nt, nt)
+        assert np.array_equal(out, oracle.jacobi(u, ff, 0.25, 2 * nt))
+
+
+# ------------------------------------------------------------ invariants ----
+@pytest.mark.parametrize("name", list(F.harmonic_fields(3, 3, 3)))
+def test_harmonic_polynomials_are_fixed_points(name):
+    nx, ny, nz = 6, 5, 7
+    u = F.harmonic_fields(nx, ny, nz)[name]
+    scale = np.abs(u).max()
+    for fn in (oracle.jacobi, oracle.gs_lex):
+        out = fn(u, None, 1.0, 5)
+        np.testing.assert_allclose(out, u, rtol=0, atol=40 * EPS * scale)
+    r, rn, _ = oracle.residual(u, None, 1.0)
+    assert rn <= 40 * EPS * scale * math.sqrt(nx * ny * nz)
+
+
+@pytest.mark.parametrize("c", [1.0, 0.5, 0.25, 2.0, 3.0])
+def test_constant_field_is_bit_exact_fixed_point(c):
+    u = np.full((7, 6, 5), c)
+    for fn in (oracle.jacobi, oracle.gs_lex):
+        assert np.array_equal(fn(u, None, 1.0, 4), u)
+    u32 = u.astype(np.float32)
+    for fn in (oracle.jacobi, oracle.gs_lex):
+        assert np.array_equal(fn(u32, None, 1.0, 4), u32)
+
+
+def test_constant_not_representable_moves():
+    """0.1: b * (6*0.1 summed) does not round back (shows the check is sharp)."""
+    u = np.full((5, 5, 5), 0.1)
+    assert not np.array_equal(oracle.jacobi(u, None, 1.0, 1), u)
+
+
+def _golden_sum_order():
+    rows = []
+    with open(os.path.join(GOLDEN, "sum_order.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            rows.append((parts[0], [float.fromhex(x) for x in parts[1:7]], float.fromhex(parts[7])))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_sum_order())
+def test_summation_order_golden(row):
+    dtype, (w, e, s, n, b, t), expected = row
+    dt = np.float64 if dtype == "f64" else np.float32
+    u = np.zeros((3, 3, 3), dtype=dt)
+    u[1, 1, 0], u[1, 1, 2], u[1, 0, 1], u[1, 2, 1], u[0, 1, 1], u[2, 1, 1] = w, e, s, n, b, t
+    for fn in (oracle.jacobi, oracle.gs_lex):
+        out = fn(u, None, 1.0, 1)
+        assert float(out[1, 1, 1]) == expected, (dtype, fn.__name__, float(out[1, 1, 1]).hex())
+
+
+# ------------------------------------------------------------- residual ----
+def test_residual_eigenrelation():
+    """A phi = lambda phi for a sine mode: r = f - lambda phi."""
+    nx, ny, nz = 8, 6, 7
+    h = 1.0 / 9
+    phi = F.sine_mode(nx, ny, nz, 2, 3, 1)
+    lam = F.eigenvalue(nx, ny, nz, 2, 3, 1, h)
+    f = np.random.default_rng(2).standard_normal(phi.shape)
+    r, rn, fn = oracle.residual(phi, f, h)
+    ref = F.interior(f) - lam * F.interior(phi)
+    np.testing.assert_allclose(F.interior(r), ref, rtol=0, atol=64 * EPS * lam)
+    assert r[0].max() == 0 and r[-1].max() == 0
+
+
+def test_residual_sparse_form_and_norm():
+    nx, ny, nz = 5, 7, 4
+    rng = np.random.default_rng(12)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    h = 0.15
+    r, rn, fn = oracle.residual(u, f, h)
+    au = (6.0 * F.interior(u) - F.neighbour_matrix(nx, ny, nz) @ F.interior(u) - F.boundary_sum(u)) / (h * h)
+    np.testing.assert_allclose(F.interior(r), F.interior(f) - au, rtol=1e-13, atol=1e-13 * np.abs(au).max())
+    exact = math.sqrt(math.fsum(float(x) ** 2 for x in F.interior(r)))
+    assert abs(rn - exact) <= 4 * EPS * exact
+    exact_f = math.sqrt(math.fsum(float(x) ** 2 for x in F.interior(f)))
+    assert abs(fn - exact_f) <= 4 * EPS * exact_f
+
+
+# ---------------------------------------------------------------- solves ----
+def _sine_rhs(n, modes, amps):
+    h = 1.0 / (n + 1)
+    f = np.zeros((n + 2,) * 3)
+    ustar = np.zeros_like(f)
+    for (p, q, r), a in zip(modes, amps):
+        phi = F.sine_mode(n, n, n, p, q, r)
+        f += a * phi
+        ustar += a * phi / F.eigenvalue(n, n, n, p, q, r, h)
+    return h, f, ustar
+
+
+@pytest.mark.parametrize("smoother", [oracle.SMOOTHER_JACOBI, oracle.SMOOTHER_GS])
+def test_solve_f64_reaches_closed_form(smoother):
+    """-Lap_h u = f with f a sum of sine modes: u* = sum a phi / lambda.  Pins the
+    sign of f and the h^2 scaling of the Poisson update."""
+    n = 10
+    h, f, ustar = _sine_rhs(n, [(1, 1, 1), (2, 1, 3), (1, 4, 2)], [1.0, -0.7, 0.4])
+    u0 = np.zeros_like(f)
+    u, rel, sweeps, ok = oracle.solve_f64(u0, f, h, smoother, 1e-12, 20000, 50)
+    assert ok and rel <= 1e-12
+    assert np.abs(u - ustar).max() <= 1e-10 * np.abs(ustar).max()
+
+
+@pytest.mark.parametrize("smoother", [oracle.SMOOTHER_JACOBI, oracle.SMOOTHER_GS])
+def test_solve_mixed_reaches_closed_form(smoother):
+    """FP32 inner sweeps + FP64 defect correction reach FP64 accuracy."""
+    n = 10
+    h, f, ustar = _sine_rhs(n, [(1, 2, 1), (3, 1, 1)], [0.9, 0.3])
+    u, rel, its, ok = oracle.solve_mixed(np.zeros_like(f), f, h, smoother, 1e-11, 200, 60)
+    assert ok and rel <= 1e-11
+    assert np.abs(u - ustar).max() <= 1e-9 * np.abs(ustar).max()
+    # one outer iteration is not enough: FP32 alone stalls near 1e-7
+    _, rel1, _, ok1 = oracle.solve_mixed(np.zeros_like(f), f, h, smoother, 1e-11, 1, 2000)
+    assert not ok1 and rel1 > 1e-9
+
+
+# ---------------------------------------------------------------- FP32 ----
+def test_f32_mode_decay_and_precision():
+    nx, ny, nz = 7, 5, 6
+    u = F.sine_mode(nx, ny, nz, 2, 1, 3)
+    mu = F.jacobi_factor(nx, ny, nz, 2, 1, 3)
+    out = oracle.jacobi(u.astype(np.float32), None, 1.0, 2)
+    assert out.dtype == np.float32
+    np.testing.assert_allclose(out.astype(np.float64), mu * mu * u, rtol=0, atol=24 * EPS32)
+    # genuinely single precision: differs from the FP64 result
+    assert not np.array_equal(out.astype(np.float64), oracle.jacobi(u, None, 1.0, 2))
+
+
+def test_f32_gs_is_lower_triangular_solve():
+    nx, ny, nz = 6, 5, 4
+    rng = np.random.default_rng(21)
+    u = rng.random((nz + 2, ny + 2, nx + 2)).astype(np.float32)
+    f = rng.standard_normal(u.shape).astype(np.float32)
+    h = 0.3
+    L, U = F.lex_split(nx, ny, nz)
+    m = (6.0 * sp.identity(nx * ny * nz) - L).tocsr()
+    u64, f64 = u.astype(np.float64), f.astype(np.float64)
+    ref = spla.spsolve_triangular(m, U @ F.interior(u64) + F.boundary_sum(u64) + (h * h) * F.interior(f64), lower=True)
+    out = oracle.gs_lex(u, f, h, 1)
+    np.testing.assert_allclose(F.interior(out), ref, rtol=64 * EPS32, atol=64 * EPS32)
