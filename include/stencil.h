@@ -1,0 +1,174 @@
+/*
+ * stencil.h - C ABI of the GB300 library for the 3D 7-point Jacobi and
+ * lexicographic Gauss-Seidel smoothers with temporal blocking.
+ *
+ * The operations follow Treibig, Wellein, Hager, "Efficient multicore-aware
+ * parallelization strategies for iterative stencil computations" (2010):
+ * the Jacobi sweep of Sec. 3 (first listing), the lexicographic Gauss-Seidel
+ * sweep of Sec. 3 (second listing), temporal blocking that applies several
+ * sweeps per pass over memory (Sec. 4) and the pipeline-parallel Gauss-Seidel
+ * that keeps the serial update order (Sec. 3, Fig. pipeline_gs).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Grid layout.  A grid with interior extents dims = {nx, ny, nz} is stored as
+ *  (nz+2)*(ny+2)*(nx+2) contiguous elements in C order, element (i, j, k) of
+ *  the padded array at offset (k*(ny+2) + j)*(nx+2) + i, i fastest (the
+ *  paper's src[k][j][i]).  Padded index 0 and n+1 in each dimension form a
+ *  one-cell Dirichlet halo that is read and never written.  The halo's edges
+ *  and corners are never read.  Extents may be 0 (nothing to do); each must
+ *  be <= 2^20 and the padded element count < 2^40.
+ *
+ *  Site update.  With S = ((((W + E) + S_) + N) + B) + T the six neighbours
+ *  added left to right in the listing's order (W = i-1, E = i+1, S_ = j-1,
+ *  N = j+1, B = k-1, T = k+1):
+ *      Laplace (f == NULL):  u' = b * S
+ *      Poisson (f != NULL):  u' = b * (S + hh * f)        hh = h*h
+ *      weighted Jacobi:      u' = a * u + b * (...)       (a != 0 only)
+ *  b = 1/6 rounded to the working precision unless given.  Poisson means
+ *  -Lap_h u = f.  Every + and * is one IEEE-754 round-to-nearest operation,
+ *  never contracted, so results are bit-identical to the serial loops.
+ *
+ *  Pointers.  u and f are DEVICE pointers (cudaMalloc'd or equivalent) owned
+ *  by the caller; the library never frees them.  Host pointers are named
+ *  out_* or say "host".
+ *
+ *  Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *  default stream).  Calls are stream-ordered and asynchronous unless they
+ *  return a value through a host out-parameter, in which case they
+ *  synchronise the stream before returning.
+ *
+ *  Errors.  Every int-returning call returns STENCIL_OK (0) or a negative
+ *  STENCIL_ERR_* code; stencil_last_error(ctx) then describes the failure.
+ *  Argument errors are detected on the host before anything is enqueued.
+ *  After STENCIL_ERR_CUDA the caller's arrays may be partially updated.
+ *
+ *  Threads.  A context may be used by one host thread at a time.
+ */
+#ifndef STENCIL_H_
+#define STENCIL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STENCIL_OK 0
+#define STENCIL_ERR_ARG (-1)           /* invalid argument (NULL, negative size, bad enum)  */
+#define STENCIL_ERR_OOM (-2)           /* workspace would exceed the budget, or cudaMalloc  */
+#define STENCIL_ERR_CUDA (-3)          /* a CUDA runtime call or kernel launch failed       */
+#define STENCIL_ERR_TIMEOUT (-4)       /* a bounded device-side wait expired                */
+#define STENCIL_ERR_NOT_CONVERGED (-5) /* a solve stopped at its cap; outputs still valid   */
+#define STENCIL_ERR_UNSUPPORTED (-6)   /* valid request this build does not implement      */
+#define STENCIL_ERR_CANCELLED (-7)     /* a served request was cancelled before admission   */
+
+#define STENCIL_JACOBI 0
+#define STENCIL_GS 1
+
+#define STENCIL_F64 0
+#define STENCIL_F32 1
+
+typedef struct stencil_ctx stencil_ctx;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context itself allocates (workspace, task tables); 0 = no cap.
+ * *out receives the context.  Fails with STENCIL_ERR_CUDA if the device
+ * cannot be used, STENCIL_ERR_ARG if out is NULL. */
+int stencil_create(stencil_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Release the context and its device memory (synchronises the device).
+ * NULL is ignored. */
+void stencil_destroy(stencil_ctx* ctx);
+
+/* Text of the last error on this context; never NULL; valid until the next
+ * call on the context.  With ctx == NULL, the last error of stencil_create. */
+const char* stencil_last_error(const stencil_ctx* ctx);
+
+/* Bytes the context currently holds on the device. */
+size_t stencil_workspace_bytes(const stencil_ctx* ctx);
+
+/* Number of CUDA kernels this context has launched so far (a counter for
+ * benchmarks: every kernel launch of every entry point adds one). */
+unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
+
+/* Tuning of one smoother call (all fields 0 = library default).
+ *  nt      sweeps applied per pass over device memory (temporal blocking,
+ *          Sec. 4); 1 = one sweep per pass.  Range 1..16.
+ *  tile_x, tile_y, tile_z
+ *          tile extents (Jacobi: thread-block tile in x, y; z chunk length.
+ *          Gauss-Seidel: task tile W, H, D).  Must be supported by the build,
+ *          else STENCIL_ERR_UNSUPPORTED.
+ *  a, b    weights of the site update; b == 0 means 1/6.  a != 0 is only
+ *          accepted by Jacobi (weighted Jacobi, a = 1 - omega, b = omega/6). */
+typedef struct stencil_params {
+  int nt;
+  int tile_x, tile_y, tile_z;
+  double a, b;
+} stencil_params;
+
+/* Jacobi smoother (Sec. 3, first listing; temporal blocking Sec. 4).
+ * Applies nsweeps >= 0 sweeps to u in place: after the call u holds the
+ * nsweeps-th Jacobi iterate (whatever the parity of nsweeps).  The second
+ * array of the out-of-place sweep comes from the context's workspace
+ * (one grid's size; STENCIL_ERR_OOM beyond the budget).  f: device pointer of
+ * the same padded shape, or NULL for f = 0.  h > 0 (used only when f != NULL).
+ * params may be NULL. */
+int stencil_jacobi(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h,
+                   int nsweeps, void* stream);
+int stencil_jacobi_ex(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h,
+                      int nsweeps, const stencil_params* params, void* stream);
+int stencil_jacobi_f32(stencil_ctx* ctx, float* u, const float* f, const int64_t dims[3], double h,
+                       int nsweeps, const stencil_params* params, void* stream);
+
+/* Lexicographic Gauss-Seidel (Sec. 3, second listing; wavefront temporal
+ * blocking Sec. 4).  In place on u, nsweeps >= 0.  Each sweep visits sites in
+ * (k, j, i) ascending order: at the moment of an update the i-1, j-1, k-1
+ * neighbours hold this sweep's values and i+1, j+1, k+1 the previous
+ * sweep's.  The parallel schedule reproduces the serial result bit for bit.
+ * The context keeps a task table per (dims, tile, nt, nsweeps) shape (a few
+ * KB to MB of device memory).  params->a must be 0. */
+int stencil_gs_lex(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h,
+                   int nsweeps, void* stream);
+int stencil_gs_lex_ex(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h,
+                      int nsweeps, const stencil_params* params, void* stream);
+int stencil_gs_lex_f32(stencil_ctx* ctx, float* u, const float* f, const int64_t dims[3], double h,
+                       int nsweeps, const stencil_params* params, void* stream);
+
+/* Residual r = f - A u, A u = (6 u - S) * (1/(h*h)), on the interior (not in
+ * the paper; the defect of -Lap_h u = f).  f may be NULL (f = 0).
+ * r_out (device, same padded shape, may be NULL): receives r on the
+ * interior; its halo is not written.
+ * out_abs (host, required): ||r||_2 over the interior, FP64.
+ * out_rel (host, may be NULL): ||r||_2 / ||f||_2 (or ||r||_2 when f is NULL
+ * or zero).  Blocking: synchronises `stream`.  The reduction has a fixed
+ * order for a given dims, so repeated calls give identical bits. */
+int residual_norm(stencil_ctx* ctx, const double* u, const double* f, const int64_t dims[3], double h,
+                  double* r_out, double* out_abs, double* out_rel, void* stream);
+
+/* Mixed-precision Poisson solve by defect correction (not in the paper):
+ *   repeat: r = f - A u (FP64); e = 0; inner_sweeps FP32 sweeps of
+ *   `smoother` (STENCIL_JACOBI or STENCIL_GS) on A e = (float) r;
+ *   u += (double) e;  until ||r||/||f|| <= rtol or max_outer iterations.
+ * u (device, FP64) is updated in place; f (device, FP64) required.
+ * Workspace: one FP64 and two FP32 grids.  out_rel / out_iters (host, may be
+ * NULL) receive the final relative residual and the outer iterations done.
+ * Returns STENCIL_ERR_NOT_CONVERGED (outputs valid) if rtol was not reached.
+ * Blocking. */
+int stencil_solve_mixed(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h,
+                        int smoother, double rtol, int max_outer, int inner_sweeps,
+                        double* out_rel, int* out_iters, void* stream);
+
+/* FP64-only solve by plain sweeps of `smoother` for comparison: the residual
+ * is checked every check_every sweeps until rel <= rtol or max_sweeps.
+ * out_sweeps (host, may be NULL) receives the sweeps done.  Blocking. */
+int stencil_solve_f64(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h,
+                      int smoother, double rtol, int max_sweeps, int check_every, const stencil_params* params,
+                      double* out_rel, int* out_sweeps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_H_ */

@@ -1,0 +1,250 @@
+"""Python binding of the C ABI in ``include/stencil.h`` (argument marshalling only).
+
+Every smoother step runs in the CUDA library ``_lib/libstencil.so``; this
+module only turns torch tensors into device pointers, shapes into ``dims``
+and the current torch stream into the ``stream`` argument.  There is no CPU
+fallback: if the library cannot be loaded, importing the functions raises.
+
+Grids are torch tensors of shape ``(nz+2, ny+2, nx+2)`` (C order, halo
+included) on a CUDA device; float64 for the FP64 entry points, float32 for
+the ``_f32`` ones.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+STENCIL_OK = 0
+STENCIL_ERR_ARG = -1
+STENCIL_ERR_OOM = -2
+STENCIL_ERR_CUDA = -3
+STENCIL_ERR_TIMEOUT = -4
+STENCIL_ERR_NOT_CONVERGED = -5
+STENCIL_ERR_UNSUPPORTED = -6
+STENCIL_ERR_CANCELLED = -7
+
+STENCIL_JACOBI = 0
+STENCIL_GS = 1
+STENCIL_F64 = 0
+STENCIL_F32 = 1
+
+_ERRNAMES = {
+    -1: "STENCIL_ERR_ARG", -2: "STENCIL_ERR_OOM", -3: "STENCIL_ERR_CUDA", -4: "STENCIL_ERR_TIMEOUT",
+    -5: "STENCIL_ERR_NOT_CONVERGED", -6: "STENCIL_ERR_UNSUPPORTED", -7: "STENCIL_ERR_CANCELLED",
+}
+
+
+class StencilError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_ERRNAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class stencil_params(ctypes.Structure):
+    _fields_ = [("nt", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
+                ("a", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_PP = ctypes.POINTER(stencil_params)
+
+_SIGS = {
+    "stencil_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t]),
+    "stencil_destroy": (None, [_P]),
+    "stencil_last_error": (ctypes.c_char_p, [_P]),
+    "stencil_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "stencil_kernel_launches": (ctypes.c_ulonglong, [_P]),
+    "stencil_jacobi": (_I, [_P, _P, _P, _I64P, _D, _I, _P]),
+    "stencil_jacobi_ex": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
+    "stencil_jacobi_f32": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
+    "stencil_gs_lex": (_I, [_P, _P, _P, _I64P, _D, _I, _P]),
+    "stencil_gs_lex_ex": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
+    "stencil_gs_lex_f32": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
+    "residual_norm": (_I, [_P, _P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
+    "stencil_solve_mixed": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
+    "stencil_solve_f64": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, _PP, ctypes.POINTER(_D), ctypes.POINTER(_I),
+                               _P]),
+}
+
+_LIB = None
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load ``_lib/libstencil.so`` (building it first if it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError("CUDA library %s is missing; run paper_1004_1741_gb300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def exported_names() -> list[str]:
+    return list(_SIGS)
+
+
+# ---------------------------------------------------------------------------
+def _dims(u: torch.Tensor):
+    if u.dim() != 3:
+        raise ValueError("grid must be 3D (nz+2, ny+2, nx+2)")
+    nz, ny, nx = (int(s) - 2 for s in u.shape)
+    return (ctypes.c_int64 * 3)(nx, ny, nz)
+
+
+def _grid(u: torch.Tensor, dtype: torch.dtype, name: str = "u"):
+    if not isinstance(u, torch.Tensor) or not u.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if u.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, u.dtype))
+    if not u.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(u.data_ptr())
+
+
+def _opt_grid(f, like: torch.Tensor, dtype: torch.dtype):
+    if f is None:
+        return None
+    if f.shape != like.shape or f.device != like.device:
+        raise ValueError("f must have u's shape and device")
+    return _grid(f, dtype, "f")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _params(nt=0, tile=(0, 0, 0), a=0.0, b=0.0):
+    p = stencil_params()
+    p.nt, p.tile_x, p.tile_y, p.tile_z, p.a, p.b = int(nt), int(tile[0]), int(tile[1]), int(tile[2]), float(a), float(b)
+    return p
+
+
+def _check(ctx, rc: int, allow=()):
+    if rc != STENCIL_OK and rc not in allow:
+        msg = load_library().stencil_last_error(ctx.handle if ctx is not None else None)
+        raise StencilError(rc, (msg or b"").decode())
+    return rc
+
+
+class Context:
+    """Owns a ``stencil_ctx`` (workspace, task tables) on one device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        rc = lib.stencil_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
+        if rc != STENCIL_OK:
+            raise StencilError(rc, (lib.stencil_last_error(None) or b"").decode())
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().stencil_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(load_library().stencil_workspace_bytes(self.handle))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(load_library().stencil_kernel_launches(self.handle))
+
+    def last_error(self) -> str:
+        return (load_library().stencil_last_error(self.handle) or b"").decode()
+
+
+# ------------------------------------------------------------ entry points --
+def stencil_jacobi(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int, *, nt: int = 0,
+                   tile=(0, 0, 0), a: float = 0.0, b: float = 0.0, stream=None) -> None:
+    """Jacobi sweeps in place on u (FP64 or FP32 by u's dtype)."""
+    lib = load_library()
+    p = _params(nt, tile, a, b)
+    if u.dtype == torch.float64:
+        rc = lib.stencil_jacobi_ex(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
+                                   float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
+    else:
+        rc = lib.stencil_jacobi_f32(ctx.handle, _grid(u, torch.float32), _opt_grid(f, u, torch.float32), _dims(u),
+                                    float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
+    _check(ctx, rc)
+
+
+def stencil_gs_lex(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int, *, nt: int = 0,
+                   tile=(0, 0, 0), stream=None) -> None:
+    """Lexicographic Gauss-Seidel sweeps in place on u (FP64 or FP32 by u's dtype)."""
+    lib = load_library()
+    p = _params(nt, tile)
+    if u.dtype == torch.float64:
+        rc = lib.stencil_gs_lex_ex(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
+                                   float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
+    else:
+        rc = lib.stencil_gs_lex_f32(ctx.handle, _grid(u, torch.float32), _opt_grid(f, u, torch.float32), _dims(u),
+                                    float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
+    _check(ctx, rc)
+
+
+def residual_norm(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, r_out: torch.Tensor | None = None,
+                  stream=None):
+    """Returns (||r||_2, ||r||_2/||f||_2) for r = f - A u (FP64); fills r_out's interior if given."""
+    lib = load_library()
+    ab, rel = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib.residual_norm(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u), float(h),
+                           _opt_grid(r_out, u, torch.float64), ctypes.byref(ab), ctypes.byref(rel), _stream(stream))
+    _check(ctx, rc)
+    return ab.value, rel.value
+
+
+def stencil_solve_mixed(ctx: Context, u: torch.Tensor, f: torch.Tensor, h: float, smoother: int, rtol: float,
+                        max_outer: int, inner_sweeps: int, stream=None):
+    """Defect correction, FP32 inner sweeps; returns (rel, outer_iters, converged)."""
+    lib = load_library()
+    rel, its = ctypes.c_double(0.0), ctypes.c_int(0)
+    rc = lib.stencil_solve_mixed(ctx.handle, _grid(u, torch.float64), _grid(f, torch.float64, "f"), _dims(u),
+                                 float(h), int(smoother), float(rtol), int(max_outer), int(inner_sweeps),
+                                 ctypes.byref(rel), ctypes.byref(its), _stream(stream))
+    _check(ctx, rc, allow=(STENCIL_ERR_NOT_CONVERGED,))
+    return rel.value, its.value, rc == STENCIL_OK
+
+
+def stencil_solve_f64(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, smoother: int, rtol: float,
+                      max_sweeps: int, check_every: int, *, nt: int = 0, tile=(0, 0, 0), stream=None):
+    """FP64 sweeps until the relative residual <= rtol; returns (rel, sweeps, converged)."""
+    lib = load_library()
+    rel, sw = ctypes.c_double(0.0), ctypes.c_int(0)
+    p = _params(nt, tile)
+    rc = lib.stencil_solve_f64(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
+                               float(h), int(smoother), float(rtol), int(max_sweeps), int(check_every),
+                               ctypes.byref(p), ctypes.byref(rel), ctypes.byref(sw), _stream(stream))
+    _check(ctx, rc, allow=(STENCIL_ERR_NOT_CONVERGED,))
+    return rel.value, sw.value, rc == STENCIL_OK

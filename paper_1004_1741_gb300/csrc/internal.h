@@ -1,0 +1,77 @@
+// Internal interfaces between the translation units of the stencil library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "stencil.h"
+#include "common.cuh"
+
+namespace stn {
+
+// One device allocation owned by the context, reused across calls.
+struct Slot {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Slots of the workspace (one buffer per purpose).
+enum SlotId {
+  SLOT_JACOBI_TMP = 0,   // second grid of the out-of-place Jacobi sweep
+  SLOT_RED_PARTIALS,     // per-block partial sums of reductions
+  SLOT_RED_RESULT,       // final reduction results (a few doubles)
+  SLOT_MIX_E32,          // FP32 correction e of the mixed solve
+  SLOT_MIX_R32,          // FP32 residual of the mixed solve
+  SLOT_MIX_TMP32,        // FP32 second grid for inner Jacobi sweeps
+  SLOT_GS_SLICES,        // Gauss-Seidel tile slices (I,J,K by I+J+K)
+  SLOT_GS_SITES,         // Gauss-Seidel intra-tile site table
+  SLOT_BATCH_DESC,       // batched-launch descriptors
+  SLOT_COUNT
+};
+
+}  // namespace stn
+
+struct stencil_ctx {
+  int device = 0;
+  size_t budget = 0;  // 0 = unlimited
+  size_t held = 0;
+  std::string err;
+  stn::Slot slots[stn::SLOT_COUNT];
+  // Gauss-Seidel geometry cache key of what SLOT_GS_SLICES / SLOT_GS_SITES hold
+  int64_t gs_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::vector<int> gs_slice_off;  // host copy of the slice prefix offsets
+  int sm_count = 0;
+  unsigned long long launches = 0;  // kernels this context has launched
+  cudaEvent_t ev = nullptr;
+};
+
+namespace stn {
+
+int set_err(stencil_ctx* ctx, int code, const char* fmt, ...);
+int cuda_err(stencil_ctx* ctx, cudaError_t e, const char* where);
+// Returns a device buffer of at least `bytes` for slot `id` (growing it if
+// needed within the budget), or nullptr with ctx->err set.
+void* ws_get(stencil_ctx* ctx, SlotId id, size_t bytes, int* status);
+int check_dims(stencil_ctx* ctx, const int64_t dims[3], Geom* g);
+
+// --- launchers (return STENCIL_* status) ---
+template <typename T>
+int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
+               const stencil_params* p, cudaStream_t st);
+template <typename T>
+int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
+           const stencil_params* p, cudaStream_t st);
+
+// Residual r = f - A u; optional FP64 r and/or FP32 r32 on the interior;
+// sums of r^2 and f^2 into the context's result slot (device) when
+// `reduce`; returns status.  `result` receives the device pointer of the two sums.
+int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Geom& g, double h,
+                    double* r_out, float* r32_out, double** result, cudaStream_t st);
+// u[interior] += (double) e[interior]
+int correct_launch(stencil_ctx* ctx, double* u, const float* e, const Geom& g, cudaStream_t st);
+
+}  // namespace stn

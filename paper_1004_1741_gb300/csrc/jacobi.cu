@@ -1,0 +1,170 @@
+// Jacobi smoother (Sec. 3, first listing): one sweep per pass over memory.
+//
+// Kernel: a 2.5D z-march.  A CTA of 32 x BY threads owns a 32 x BY tile of
+// (x, y) columns and a chunk of z-planes.  Each thread keeps its own column's
+// planes k-1, k, k+1 in registers (the paper's "three planes in cache" of
+// Fig. stencil_mapping, here in the register file), the current plane is
+// staged in shared memory (double-buffered, one __syncthreads per plane) for
+// the four in-plane neighbours, and halo columns/rows of the tile are loaded
+// by the edge threads.  Every lane of every warp produces an output site, so
+// the FP64 pipe executes exactly the 6 (Laplace) or 8 (Poisson) operations
+// of a site update per lattice update and nothing else.
+//
+// Temporal blocking (nt > 1 sweeps per pass) is implemented by the
+// skewed-tile task scheduler in tb_tasks.cu.
+#include "internal.h"
+
+namespace stn {
+
+template <typename T, class Ar, bool HAS_F, bool WEIGHTED, int BY>
+__global__ void __launch_bounds__(32 * BY) jacobi_zmarch_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                                                const T* __restrict__ f, Geom g, int zchunk,
+                                                                Coef<T> c) {
+  __shared__ T sm[2][BY + 2][32 + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * 32 + tx;
+  const int y = blockIdx.y * BY + ty;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(g.nz, z0 + zchunk);
+  if (z0 >= z1) return;  // uniform over the block
+  const bool inside = (x <= g.nx) && (y <= g.ny);  // own column lies in the interior or the +1 halo
+  const bool active = (x < g.nx) && (y < g.ny);    // own column is an interior column
+  // halo duties (each at most one extra column or row)
+  const bool hw = (tx == 0) && (y <= g.ny);                     // column x-1 (>= -1)
+  const bool he = (tx == 31) && (x + 1 <= g.nx) && (y <= g.ny);  // column x+1
+  const bool hs = (ty == 0) && (x <= g.nx);                     // row y-1 (>= -1)
+  const bool hn = (ty == BY - 1) && (y + 1 <= g.ny) && (x <= g.nx);
+  const int64_t sy = g.sy;
+  const int64_t col = inside ? g.at(x, y, -1) : 0;  // padded offset of (x, y) at plane -1
+  const int64_t colw = hw ? g.at(x - 1, y, -1) : 0;
+  const int64_t cole = he ? g.at(x + 1, y, -1) : 0;
+  const int64_t cols = hs ? g.at(x, y - 1, -1) : 0;
+  const int64_t coln = hn ? g.at(x, y + 1, -1) : 0;
+
+  // registers: planes z-1, z, z+1 of the own column (plane index p at offset (p+1)*sy)
+  T below = inside ? src[col + (int64_t)(z0)*sy] : T(0);
+  T cur = inside ? src[col + (int64_t)(z0 + 1) * sy] : T(0);
+  T above = inside ? src[col + (int64_t)(z0 + 2) * sy] : T(0);
+  int buf = 0;
+  for (int z = z0; z < z1; ++z) {
+    const int64_t pz = (int64_t)(z + 1) * sy;
+    sm[buf][ty + 1][tx + 1] = cur;
+    if (hw) sm[buf][ty + 1][0] = src[colw + pz];
+    if (he) sm[buf][ty + 1][33] = src[cole + pz];
+    if (hs) sm[buf][0][tx + 1] = src[cols + pz];
+    if (hn) sm[buf][BY + 1][tx + 1] = src[coln + pz];
+    // prefetch plane z+2 (exists up to the top halo plane nz)
+    T next = (inside && z + 2 <= g.nz) ? src[col + pz + 2 * sy] : T(0);
+    T fv = T(0);
+    if (HAS_F && active) fv = f[col + pz];
+    __syncthreads();
+    if (active) {
+      T v = site_update<T, Ar, HAS_F, WEIGHTED>(sm[buf][ty + 1][tx], sm[buf][ty + 1][tx + 2], sm[buf][ty][tx + 1],
+                                                sm[buf][ty + 2][tx + 1], below, above, fv, cur, c);
+      dst[col + pz] = v;
+    }
+    below = cur;
+    cur = above;
+    above = next;
+    buf ^= 1;
+  }
+}
+
+template <typename T>
+struct JacobiLaunch {
+  template <class Ar, bool HAS_F, bool WEIGHTED, int BY>
+  static cudaError_t go(const T* src, T* dst, const T* f, const Geom& g, int zchunk, Coef<T> c, cudaStream_t st) {
+    dim3 block(32, BY);
+    dim3 grid((g.nx + 31) / 32, (g.ny + BY - 1) / BY, (g.nz + zchunk - 1) / zchunk);
+    jacobi_zmarch_kernel<T, Ar, HAS_F, WEIGHTED, BY><<<grid, block, 0, st>>>(src, dst, f, g, zchunk, c);
+    return cudaGetLastError();
+  }
+  template <class Ar, int BY>
+  static cudaError_t pick(const T* src, T* dst, const T* f, const Geom& g, int zchunk, Coef<T> c, bool weighted,
+                          cudaStream_t st) {
+    if (f) {
+      return weighted ? go<Ar, true, true, BY>(src, dst, f, g, zchunk, c, st)
+                      : go<Ar, true, false, BY>(src, dst, f, g, zchunk, c, st);
+    }
+    return weighted ? go<Ar, false, true, BY>(src, dst, f, g, zchunk, c, st)
+                    : go<Ar, false, false, BY>(src, dst, f, g, zchunk, c, st);
+  }
+};
+
+// One sweep src -> dst (both hold the same Dirichlet halo).
+template <typename T>
+cudaError_t jacobi_sweep(const T* src, T* dst, const T* f, const Geom& g, int by, int zchunk, Coef<T> c,
+                         bool weighted, cudaStream_t st) {
+  using Ar = typename DefaultArith<T>::type;
+  switch (by) {
+    case 4: return JacobiLaunch<T>::template pick<Ar, 4>(src, dst, f, g, zchunk, c, weighted, st);
+    case 16: return JacobiLaunch<T>::template pick<Ar, 16>(src, dst, f, g, zchunk, c, weighted, st);
+    default: return JacobiLaunch<T>::template pick<Ar, 8>(src, dst, f, g, zchunk, c, weighted, st);
+  }
+}
+
+template <typename T>
+int tb_jacobi_run(stencil_ctx* ctx, T* u, T* tmp, const T* f, const Geom& g, double h, int nsweeps,
+                  const stencil_params* p, cudaStream_t st);
+
+template <typename T>
+static Coef<T> make_coef(double h, const stencil_params* p) {
+  Coef<T> c;
+  double b = (p && p->b != 0.0) ? p->b : 1.0 / 6.0;
+  c.a = (T)(p ? p->a : 0.0);
+  c.b = (T)b;
+  c.hh = (T)(h * h);
+  return c;
+}
+
+template <typename T>
+int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps, const stencil_params* p,
+               cudaStream_t st) {
+  if (nsweeps == 0 || g.nx == 0 || g.ny == 0 || g.nz == 0) return STENCIL_OK;
+  const size_t bytes = (size_t)g.sy * (size_t)(g.nz + 2) * sizeof(T);
+  int status = STENCIL_OK;
+  T* tmp = (T*)ws_get(ctx, SLOT_JACOBI_TMP, bytes, &status);
+  if (!tmp) return status;
+  const int nt = (p && p->nt > 0) ? p->nt : 1;
+  if (nt > 1) return tb_jacobi_run<T>(ctx, u, tmp, f, g, h, nsweeps, p, st);
+  const bool weighted = p && p->a != 0.0;
+  Coef<T> c = make_coef<T>(h, p);
+  int by = (p && p->tile_y) ? p->tile_y : 8;
+  if (by != 4 && by != 8 && by != 16)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Jacobi tile_y = %d (supported 4, 8, 16)", by);
+  if (p && p->tile_x && p->tile_x != 32)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Jacobi tile_x = %d (supported 32)", p->tile_x);
+  int zchunk = (p && p->tile_z) ? p->tile_z : 0;
+  if (zchunk <= 0) {
+    // enough CTAs for ~8 waves of resident CTAs, chunks of at least 16 planes
+    long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + by - 1) / by);
+    long long want = (long long)ctx->sm_count * (2048 / (32 * by)) * 8;
+    long long chunks = (want + cols - 1) / cols;
+    zchunk = (int)((g.nz + chunks - 1) / chunks);
+    if (zchunk < 16) zchunk = 16;
+  }
+  // the workspace grid carries the same halo as u
+  cudaError_t e = cudaMemcpyAsync(tmp, u, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaMemcpyAsync(jacobi halo)");
+  // ping-pong; with an odd count the first sweep reads the copy so the last lands in u
+  T* a = (nsweeps % 2) ? tmp : u;
+  T* b = (nsweeps % 2) ? u : tmp;
+  for (int s = 0; s < nsweeps; ++s) {
+    e = jacobi_sweep<T>(a, b, f, g, by, zchunk, c, weighted, st);
+    ctx->launches++;
+    if (e != cudaSuccess) return cuda_err(ctx, e, "jacobi_zmarch_kernel launch");
+    T* sw = a; a = b; b = sw;
+  }
+  return STENCIL_OK;
+}
+
+template int jacobi_run<double>(stencil_ctx*, double*, const double*, const Geom&, double, int,
+                                const stencil_params*, cudaStream_t);
+template int jacobi_run<float>(stencil_ctx*, float*, const float*, const Geom&, double, int, const stencil_params*,
+                               cudaStream_t);
+template cudaError_t jacobi_sweep<double>(const double*, double*, const double*, const Geom&, int, int, Coef<double>,
+                                          bool, cudaStream_t);
+template cudaError_t jacobi_sweep<float>(const float*, float*, const float*, const Geom&, int, int, Coef<float>, bool,
+                                         cudaStream_t);
+
+}  // namespace stn

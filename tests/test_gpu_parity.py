@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+FP64 and FP32 smoother results must be bit-exact (fixed expression order, no
+contraction on either side).  Residual norms differ only in the reduction
+order and must agree to 1e-12 relative."""
+import concurrent.futures as cf
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_1741_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only hosts skip at collection
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1004_1741_gb300 import capi  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = capi.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _run(ctx, fn, u0, f0, h, nsweeps, **kw):
+    u = _dev(u0)
+    fn(ctx, u, _dev(f0), h, nsweeps, **kw)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+def _assert_exact(got, ref, what):
+    if not np.array_equal(got, ref):
+        bad = np.argwhere(got != ref)
+        i = tuple(bad[0])
+        raise AssertionError("%s: %d sites differ, first %s got %r want %r" % (what, len(bad), i, got[i], ref[i]))
+
+
+RAGGED = [(37, 19, 23), (1, 1, 1), (1, 1, 9), (9, 1, 1), (33, 9, 50), (64, 17, 5), (3, 70, 4)]
+
+
+# ------------------------------------------------------------------ Jacobi --
+def test_config1_laplace64_jacobi_full_field(ctx):
+    """64^3 Laplace, halo U[0,1) seed 0, interior 0, 10 sweeps: full field bit-exact."""
+    u0 = W.laplace_64()
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u0, None, 1.0, 10), oracle.jacobi(u0, None, 1.0, 10), "config1")
+
+
+@pytest.mark.parametrize("dims", RAGGED)
+@pytest.mark.parametrize("nsweeps", [1, 2, 5])
+@pytest.mark.parametrize("poisson", [False, True])
+def test_jacobi_f64_ragged(ctx, dims, nsweeps, poisson):
+    u0, f0 = W.random_grid(*dims, seed=sum(dims) + nsweeps, with_f=poisson)
+    h = W.grid_h(*dims)
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, h, nsweeps), oracle.jacobi(u0, f0, h, nsweeps), "jacobi f64")
+
+
+@pytest.mark.parametrize("tile", [(32, 4, 7), (32, 16, 3), (0, 8, 1), (0, 0, 0)])
+def test_jacobi_f64_tiles_and_zchunks(ctx, tile):
+    u0, f0 = W.random_grid(45, 38, 29, seed=5, with_f=True)
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.1, 3, tile=tile), oracle.jacobi(u0, f0, 0.1, 3), str(tile))
+
+
+def test_jacobi_weighted(ctx):
+    u0, f0 = W.random_grid(30, 20, 10, seed=8, with_f=True)
+    a, b = 1.0 - 0.8, 0.8 / 6.0
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.05, 4, a=a, b=b),
+                  oracle.jacobi(u0, f0, 0.05, 4, a=a, b=b), "weighted")
+
+
+@pytest.mark.parametrize("dims", [(37, 19, 23), (64, 64, 8), (1, 5, 3)])
+def test_jacobi_f32_bit_exact(ctx, dims):
+    u0, f0 = W.random_grid(*dims, seed=3, dtype=np.float32, with_f=True)
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.02, 3), oracle.jacobi(u0, f0, 0.02, 3), "jacobi f32")
+
+
+def test_jacobi_zero_sweeps_and_empty(ctx):
+    u0, _ = W.random_grid(7, 6, 5, seed=1)
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u0, None, 1.0, 0), u0, "zero sweeps")
+    e0 = np.random.default_rng(0).random((2, 5, 6))  # nz = 0
+    _assert_exact(_run(ctx, capi.stencil_jacobi, e0, None, 1.0, 3), e0, "empty")
+
+
+# ------------------------------------------------------------ Gauss-Seidel --
+@pytest.mark.parametrize("dims", RAGGED)
+@pytest.mark.parametrize("nsweeps", [1, 2, 5])
+def test_gs_f64_ragged(ctx, dims, nsweeps):
+    u0, f0 = W.random_grid(*dims, seed=11 + nsweeps, with_f=True)
+    h = W.grid_h(*dims)
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, h, nsweeps), oracle.gs_lex(u0, f0, h, nsweeps), "gs f64")
+
+
+@pytest.mark.parametrize("tile", [(16, 16, 16), (8, 8, 8), (32, 8, 8), (32, 16, 16)])
+@pytest.mark.parametrize("nt", [1, 2, 3, 4])
+def test_gs_f64_tiles_temporal(ctx, tile, nt):
+    u0, f0 = W.random_grid(45, 38, 29, seed=nt, with_f=True)
+    ns = 2 * nt + 1
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.07, ns, nt=nt, tile=tile), oracle.gs_lex(u0, f0, 0.07, ns),
+                  "gs %s nt=%d" % (tile, nt))
+
+
+@pytest.mark.parametrize("nt", [1, 4, 8])
+def test_gs_f32_temporal(ctx, nt):
+    u0, f0 = W.random_grid(40, 33, 27, seed=9, dtype=np.float32, with_f=True)
+    ns = 2 * nt + 3
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.03, ns, nt=nt), oracle.gs_lex(u0, f0, 0.03, ns), "gs f32")
+
+
+def test_gs_laplace_config1(ctx):
+    u0 = W.laplace_64()
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, None, 1.0, 10), oracle.gs_lex(u0, None, 1.0, 10), "gs config1")
+
+
+# ---------------------------------------------------------------- residual --
+@pytest.mark.parametrize("dims", [(37, 19, 23), (1, 1, 1), (64, 64, 64)])
+def test_residual_norm(ctx, dims):
+    u0, f0 = W.random_grid(*dims, seed=4, with_f=True)
+    h = W.grid_h(*dims)
+    r = torch.zeros(u0.shape, dtype=torch.float64, device=DEV)
+    ab, rel = capi.residual_norm(ctx, _dev(u0), _dev(f0), h, r_out=r)
+    r_ref, ab_ref, fn_ref = oracle.residual(u0, f0, h)
+    _assert_exact(r.cpu().numpy(), r_ref, "r")
+    assert abs(ab - ab_ref) <= 1e-12 * ab_ref
+    assert abs(rel - ab_ref / fn_ref) <= 1e-12 * (ab_ref / fn_ref)
+    ab2, _ = capi.residual_norm(ctx, _dev(u0), _dev(f0), h)
+    assert ab2 == ab  # fixed reduction order
+
+
+# ------------------------------------------------------------------ solves --
+@pytest.mark.parametrize("smoother", [capi.STENCIL_JACOBI, capi.STENCIL_GS])
+def test_solve_mixed_fixed_iterations_bit_exact(ctx, smoother):
+    """With rtol = 0 both sides run max_outer iterations: u must match bit for bit."""
+    p = W.sine_modes_problem(24, seed=4)
+    u = torch.zeros(p.f.shape, dtype=torch.float64, device=DEV)
+    rel, its, ok = capi.stencil_solve_mixed(ctx, u, _dev(p.f), p.h, smoother, 0.0, 3, 7)
+    uref, rel_ref, its_ref, _ = oracle.solve_mixed(np.zeros_like(p.f), p.f, p.h, smoother, 0.0, 3, 7)
+    assert its == its_ref == 3 and not ok
+    _assert_exact(u.cpu().numpy(), uref, "mixed u")
+    assert abs(rel - rel_ref) <= 1e-12 * rel_ref
+
+
+def test_solve_mixed_converges(ctx):
+    p = W.sine_modes_problem(16, seed=4, noise_sigma=0.0)
+    u = torch.zeros(p.f.shape, dtype=torch.float64, device=DEV)
+    rel, its, ok = capi.stencil_solve_mixed(ctx, u, _dev(p.f), p.h, capi.STENCIL_GS, 1e-10, 400, 50)
+    assert ok and rel <= 1e-10
+
+
+def test_solve_f64_matches_oracle(ctx):
+    p = W.sine_modes_problem(20, seed=4)
+    u = torch.zeros(p.f.shape, dtype=torch.float64, device=DEV)
+    rel, sw, ok = capi.stencil_solve_f64(ctx, u, _dev(p.f), p.h, capi.STENCIL_GS, 0.0, 30, 10)
+    uref, rel_ref, sw_ref, _ = oracle.solve_f64(np.zeros_like(p.f), p.f, p.h, oracle.SMOOTHER_GS, 0.0, 30, 10)
+    assert sw == sw_ref == 30
+    _assert_exact(u.cpu().numpy(), uref, "solve_f64 u")
+
+
+# ------------------------------------------------------------- arguments --
+def test_argument_errors(ctx):
+    u = torch.zeros((5, 5, 5), dtype=torch.float64, device=DEV)
+    with pytest.raises(capi.StencilError) as e:
+        capi.stencil_jacobi(ctx, u, None, 1.0, -1)
+    assert e.value.code == capi.STENCIL_ERR_ARG
+    with pytest.raises(capi.StencilError) as e:
+        capi.stencil_gs_lex(ctx, u, None, 0.0, 1)
+    assert e.value.code == capi.STENCIL_ERR_ARG
+    with pytest.raises(capi.StencilError) as e:
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 1, tile=(7, 7, 7))
+    assert e.value.code == capi.STENCIL_ERR_UNSUPPORTED
+    with pytest.raises(capi.StencilError) as e:
+        capi.stencil_jacobi(ctx, u, None, 1.0, 1, nt=17)
+    assert e.value.code == capi.STENCIL_ERR_ARG
+
+
+def test_budget_oom():
+    small = capi.Context(0, hbm_budget_bytes=1024)
+    u = torch.zeros((66, 66, 66), dtype=torch.float64, device=DEV)
+    with pytest.raises(capi.StencilError) as e:
+        capi.stencil_jacobi(small, u, None, 1.0, 2)
+    assert e.value.code == capi.STENCIL_ERR_OOM
+    small.close()
+
+
+# ------------------------------------------------- full size (400^3 FP64) --
+@pytest.mark.parametrize("smoother", ["jacobi", "gs"])
+def test_full_size_400_bench_config(ctx, smoother):
+    """The benchmark grid (400^3 FP64, halo seed 1, interior seed 2) in the
+    launch configuration bench.py times, 100 sweeps: full field bit-exact."""
+    import bench
+
+    cfg = bench.HEADLINE[smoother]
+    u0 = W.laplace_cube(400)
+    with cf.ThreadPoolExecutor(1) as ex:  # the oracle releases the GIL inside C
+        fut = ex.submit(oracle.jacobi if smoother == "jacobi" else oracle.gs_lex, u0, None, 1.0, 100)
+        fn = capi.stencil_jacobi if smoother == "jacobi" else capi.stencil_gs_lex
+        got = _run(ctx, fn, u0, None, 1.0, 100, nt=cfg["nt"], tile=cfg["tile"])
+        ref = fut.result()
+    _assert_exact(got, ref, "400^3 %s" % smoother)
