@@ -387,6 +387,28 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
             "d2h_bytes_per_step": nbytes, "steps": steps}
 
 
+def run_case(args):
+    """One smoother on an n^3 FP64 grid (halo seed 1, interior seed 2), --repeat calls
+    of --sweeps sweeps: the small case for profiler captures."""
+    import torch
+
+    from paper_1004_1741_gb300 import capi, workloads
+
+    ctx = capi.Context(0)
+    u = torch.from_numpy(workloads.laplace_cube(args.n)).to("cuda")
+    dt = torch.float32 if args.dtype == "f32" else torch.float64
+    u = u.to(dt)
+    fn = capi.stencil_jacobi if args.case == "jacobi" else capi.stencil_gs_lex
+    tile = tuple(int(x) for x in args.tile.split(",")) if args.tile else (0, 0, 0)
+    for _ in range(args.repeat):
+        fn(ctx, u, None, 1.0, args.sweeps, nt=args.nt, tile=tile)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "n": args.n, "sweeps": args.sweeps, "nt": args.nt, "repeat": args.repeat,
+                      "launches": ctx.kernel_launches}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,7 +418,16 @@ def main():
     ap.add_argument("--skip-nt-sweep", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--case", choices=["jacobi", "gs"], help="run one smoother only (profiling case)")
+    ap.add_argument("--n", type=int, default=320)
+    ap.add_argument("--sweeps", type=int, default=8)
+    ap.add_argument("--nt", type=int, default=1)
+    ap.add_argument("--tile", default="")
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--repeat", type=int, default=1)
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
