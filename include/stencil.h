@@ -101,11 +101,15 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          Gauss-Seidel: task tile W, H, D).  Must be supported by the build,
  *          else STENCIL_ERR_UNSUPPORTED.
  *  a, b    weights of the site update; b == 0 means 1/6.  a != 0 is only
- *          accepted by Jacobi (weighted Jacobi, a = 1 - omega, b = omega/6). */
+ *          accepted by Jacobi (weighted Jacobi, a = 1 - omega, b = omega/6).
+ *  variant kernel variant (Gauss-Seidel): 0 = default, 1 = tile staged in
+ *          shared memory, 2 = tile updated in place through the L1 cache.
+ *          Every variant gives the same bits. */
 typedef struct stencil_params {
   int nt;
   int tile_x, tile_y, tile_z;
   double a, b;
+  int variant;
 } stencil_params;
 
 /* Jacobi smoother (Sec. 3, first listing; temporal blocking Sec. 4).

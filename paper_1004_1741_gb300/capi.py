@@ -46,7 +46,7 @@ class StencilError(RuntimeError):
 
 class stencil_params(ctypes.Structure):
     _fields_ = [("nt", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
-                ("a", ctypes.c_double), ("b", ctypes.c_double)]
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("variant", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -131,9 +131,10 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _params(nt=0, tile=(0, 0, 0), a=0.0, b=0.0):
+def _params(nt=0, tile=(0, 0, 0), a=0.0, b=0.0, variant=0):
     p = stencil_params()
     p.nt, p.tile_x, p.tile_y, p.tile_z, p.a, p.b = int(nt), int(tile[0]), int(tile[1]), int(tile[2]), float(a), float(b)
+    p.variant = int(variant)
     return p
 
 
@@ -201,10 +202,10 @@ def stencil_jacobi(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: flo
 
 
 def stencil_gs_lex(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int, *, nt: int = 0,
-                   tile=(0, 0, 0), stream=None) -> None:
+                   tile=(0, 0, 0), variant: int = 0, stream=None) -> None:
     """Lexicographic Gauss-Seidel sweeps in place on u (FP64 or FP32 by u's dtype)."""
     lib = load_library()
-    p = _params(nt, tile)
+    p = _params(nt, tile, variant=variant)
     if u.dtype == torch.float64:
         rc = lib.stencil_gs_lex_ex(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
                                    float(h), int(nsweeps), ctypes.byref(p), _stream(stream))

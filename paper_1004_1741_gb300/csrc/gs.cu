@@ -26,17 +26,25 @@
 namespace stn {
 
 constexpr int GS_THREADS = 256;
+constexpr int GS_MAXPOS = 8;     // box-plane positions per thread: (W+nt+1)(H+nt+1) <= 8*256
+constexpr int GS_MAXLEVELS = 128;  // tile-local levels W+H+D-3+ns <= 128
+
+// Site table of the tile-local levels (built on the host, see ensure_sites).
+struct SiteTable {
+  const uint32_t* coords;  // packed (ii, jj, kk, s)
+  const uint16_t* lis;     // shared-memory index of the site inside the staged box
+  const int* off;          // level offsets, per ns one block of W+H+D-2+ns entries
+  const int* base;         // base[ns]: first entry of ns's block in off
+};
 
 template <typename T, class Ar, bool HAS_F, int W, int H, int D>
 __global__ void __launch_bounds__(GS_THREADS) gs_task_kernel(T* __restrict__ u, const T* __restrict__ f, Geom g,
                                                               Coef<T> c, const uint64_t* __restrict__ slices,
-                                                              const int* __restrict__ slice_off,
-                                                              const uint32_t* __restrict__ sites,
-                                                              const int* __restrict__ site_off,
-                                                              const int* __restrict__ site_base, TileGeom tg,
-                                                              int level) {
+                                                              const int* __restrict__ slice_off, SiteTable tb,
+                                                              TileGeom tg, int level) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
+  __shared__ int s_off[GS_MAXLEVELS + 1];
   const int tid = threadIdx.x;
 
   // ---- which task: blocks of this level enumerate the passes' slices in order
@@ -57,54 +65,138 @@ __global__ void __launch_bounds__(GS_THREADS) gs_task_kernel(T* __restrict__ u, 
   const int ns = min(tg.nt, tg.nsweeps - p * tg.nt);
   const int X0 = I * W, Y0 = J * H, Z0 = K * D;
 
-  // ---- stage the box [X0-ns, X0+W] x [Y0-ns, Y0+H] x [Z0-ns, Z0+D]
+  // ---- the staged box [X0-ns, X0+W] x [Y0-ns, Y0+H] x [Z0-ns, Z0+D]
   const int bw = W + ns + 1, bh = H + ns + 1, bd = D + ns + 1;
+  const int plane = bw * bh;
   const int bx0 = X0 - ns, by0 = Y0 - ns, bz0 = Z0 - ns;
-  const int nbox = bw * bh * bd;
-  for (int e = tid; e < nbox; e += GS_THREADS) {
-    const int lx = e % bw;
-    const int r = e / bw;
-    const int ly = r % bh;
-    const int lz = r / bh;
-    const int x = bx0 + lx, y = by0 + ly, z = bz0 + lz;
-    if (x >= -1 && x <= g.nx && y >= -1 && y <= g.ny && z >= -1 && z <= g.nz) sm[e] = u[g.at(x, y, z)];
+  const int nlv = W + H + D - 3 + ns;
+  const int* so = tb.off + tb.base[ns];
+  for (int l = tid; l <= nlv; l += GS_THREADS) s_off[l] = so[l];
+  // every site this task updates is an interior site: no bounds checks per site
+  const bool full = (X0 - ns + 1 >= 0) && (Y0 - ns + 1 >= 0) && (Z0 - ns + 1 >= 0) && (X0 + W <= g.nx) &&
+                    (Y0 + H <= g.ny) && (Z0 + D <= g.nz);
+
+  // stage: each thread owns fixed (x, y) positions of the box plane and walks z
+  const int zlo = max(0, -1 - bz0), zhi = min(bd - 1, g.nz - bz0);  // box planes inside [-1, nz]
+#pragma unroll
+  for (int r = 0; r < GS_MAXPOS; ++r) {
+    const int e = tid + r * GS_THREADS;
+    if (e >= plane) break;
+    const int ly = e / bw, lx = e - ly * bw;
+    const int x = bx0 + lx, y = by0 + ly;
+    if (x < -1 || x > g.nx || y < -1 || y > g.ny) continue;
+    if (zlo > zhi) continue;
+    const T* src = u + g.at(x, y, bz0 + zlo);
+    T* dst = sm + e + zlo * plane;
+#pragma unroll 4
+    for (int lz = 0; lz <= zhi - zlo; ++lz) dst[lz * plane] = src[(int64_t)lz * g.sy];
   }
   __syncthreads();
 
   // ---- tile-local levels ii+jj+kk-s, from -(ns-1) to W+H+D-3
-  const int nlv = W + H + D - 2 + ns - 1;
-  const int* so = site_off + site_base[ns];
-  const int plane = bw * bh;
   for (int lv = 0; lv < nlv; ++lv) {
-    const int beg = so[lv], end = so[lv + 1];
-    for (int e = beg + tid; e < end; e += GS_THREADS) {
-      const uint32_t s = sites[e];
-      const int sw = (int)(s >> 24);
-      const int x = X0 - sw + (int)(s & 0xFF);
-      const int y = Y0 - sw + (int)((s >> 8) & 0xFF);
-      const int z = Z0 - sw + (int)((s >> 16) & 0xFF);
-      if (x >= 0 && x < g.nx && y >= 0 && y < g.ny && z >= 0 && z < g.nz) {
-        const int li = ((z - bz0) * bh + (y - by0)) * bw + (x - bx0);
-        T fv = T(0);
+    const int beg = s_off[lv], end = s_off[lv + 1];
+    // A level's sites go to consecutive threads starting at a warp that rotates
+    // with the level and the CTA, so small levels do not all land on warp 0 and
+    // thereby on one SM sub-partition's FP64 pipe.
+    int t = tid - (((int)blockIdx.x + lv) & 7) * 32;
+    if (t < 0) t += GS_THREADS;
+    for (int e = beg + t; e < end; e += GS_THREADS) {
+      const int li = tb.lis[e];
+      T fv = T(0);
+      if (!full || HAS_F) {
+        const uint32_t s = tb.coords[e];
+        const int sw = (int)(s >> 24);
+        const int x = X0 - sw + (int)(s & 0xFF);
+        const int y = Y0 - sw + (int)((s >> 8) & 0xFF);
+        const int z = Z0 - sw + (int)((s >> 16) & 0xFF);
+        if (!full && (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz)) continue;
         if (HAS_F) fv = f[g.at(x, y, z)];
-        sm[li] = site_update<T, Ar, HAS_F, false>(sm[li - 1], sm[li + 1], sm[li - bw], sm[li + bw], sm[li - plane],
-                                                  sm[li + plane], fv, T(0), c);
       }
+      sm[li] = site_update<T, Ar, HAS_F, false>(sm[li - 1], sm[li + 1], sm[li - bw], sm[li + bw], sm[li - plane],
+                                                sm[li + plane], fv, T(0), c);
     }
     __syncthreads();
   }
 
-  // ---- write back every site this task updated (its last value here)
-  for (int e = tid; e < nbox; e += GS_THREADS) {
-    const int lx = e % bw;
-    const int r = e / bw;
-    const int ly = r % bh;
-    const int lz = r / bh;
-    const int x = bx0 + lx, y = by0 + ly, z = bz0 + lz;
-    if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz) continue;
-    const int s_lo = max(max(X0 - x, Y0 - y), max(Z0 - z, 0));
-    const int s_hi = min(min(X0 + W - x, Y0 + H - y), min(Z0 + D - z, ns));
-    if (s_lo < s_hi) u[g.at(x, y, z)] = sm[e];
+  // ---- write back every site this task updated (its last value here).  Site
+  // (x, y, z) is updated at the pass-local sweeps s with X0-s <= x < X0+W-s (same
+  // in y, z) and 0 <= s < ns; the xy part of that range is fixed per position.
+#pragma unroll
+  for (int r = 0; r < GS_MAXPOS; ++r) {
+    const int e = tid + r * GS_THREADS;
+    if (e >= plane) break;
+    const int ly = e / bw, lx = e - ly * bw;
+    const int x = bx0 + lx, y = by0 + ly;
+    if (x < 0 || x >= g.nx || y < 0 || y >= g.ny) continue;
+    const int a = max(max(X0 - x, Y0 - y), 0);
+    const int bb = min(min(X0 + W - x, Y0 + H - y), ns);
+    if (a >= bb) continue;
+    // z with max(a, Z0-z) < min(bb, Z0+D-z): Z0-bb < z < Z0+D-a, inside the interior
+    const int z_lo = max(Z0 - bb + 1, 0), z_hi = min(Z0 + D - a - 1, g.nz - 1);
+    T* dst = u + g.at(x, y, 0);
+    const T* src = sm + e;
+#pragma unroll 4
+    for (int z = z_lo; z <= z_hi; ++z) dst[(int64_t)z * g.sy] = src[(z - bz0) * plane];
+  }
+}
+
+// Direct variant: the same schedule, but the task updates the grid in place
+// through the L1 cache instead of staging a box in shared memory.  A site
+// written at tile level lv is read at level lv+1 by threads of the same CTA
+// after the barrier (global writes of a CTA are visible to the CTA after
+// __syncthreads); everything written by other tasks comes from earlier
+// launches.  Without a shared-memory box, up to eight CTAs fit on an SM,
+// which keeps enough independent FP64 chains in flight to fill the SM's
+// FP64 pipe.
+template <typename T, class Ar, bool HAS_F, int W, int H, int D>
+__global__ void __launch_bounds__(GS_THREADS) gs_direct_kernel(T* u, const T* __restrict__ f, Geom g, Coef<T> c,
+                                                                const uint64_t* __restrict__ slices,
+                                                                const int* __restrict__ slice_off, SiteTable tb,
+                                                                TileGeom tg, int level) {
+  __shared__ int s_off[GS_MAXLEVELS + 1];
+  const int tid = threadIdx.x;
+  int b = blockIdx.x;
+  int p = level / tg.cstride;
+  if (p > tg.npass - 1) p = tg.npass - 1;
+  int sigma = level - tg.cstride * p;
+  for (;;) {
+    int cnt = (sigma <= tg.sigma_max) ? slice_off[sigma + 1] - slice_off[sigma] : 0;
+    if (b < cnt) break;
+    b -= cnt;
+    --p;
+    sigma += tg.cstride;
+    if (p < 0) return;
+  }
+  int I, J, K;
+  unpack_tile(slices[slice_off[sigma] + b], &I, &J, &K);
+  const int ns = min(tg.nt, tg.nsweeps - p * tg.nt);
+  const int X0 = I * W, Y0 = J * H, Z0 = K * D;
+  const int nlv = W + H + D - 3 + ns;
+  const int* so = tb.off + tb.base[ns];
+  for (int l = tid; l <= nlv; l += GS_THREADS) s_off[l] = so[l];
+  const bool full = (X0 - ns + 1 >= 0) && (Y0 - ns + 1 >= 0) && (Z0 - ns + 1 >= 0) && (X0 + W <= g.nx) &&
+                    (Y0 + H <= g.ny) && (Z0 + D <= g.nz);
+  const int64_t sx = g.sx, sy = g.sy;
+  T* ut = u + g.at(X0, Y0, Z0);  // site (ii, jj, kk) of sweep s at ut[(kk-s)*sy + (jj-s)*sx + (ii-s)]
+  __syncthreads();
+  for (int lv = 0; lv < nlv; ++lv) {
+    const int beg = s_off[lv], end = s_off[lv + 1];
+    int t = tid - (((int)blockIdx.x + lv) & 7) * 32;
+    if (t < 0) t += GS_THREADS;
+    for (int e = beg + t; e < end; e += GS_THREADS) {
+      const uint32_t s = tb.coords[e];
+      const int sw = (int)(s >> 24);
+      const int dx = (int)(s & 0xFF) - sw, dy = (int)((s >> 8) & 0xFF) - sw, dz = (int)((s >> 16) & 0xFF) - sw;
+      if (!full && (X0 + dx < 0 || X0 + dx >= g.nx || Y0 + dy < 0 || Y0 + dy >= g.ny || Z0 + dz < 0 ||
+                    Z0 + dz >= g.nz))
+        continue;
+      T* q = ut + ((int64_t)dz * sy + (int64_t)dy * sx + dx);
+      T fv = T(0);
+      if (HAS_F) fv = f[q - u];
+      *q = site_update<T, Ar, HAS_F, false>(q[-1], q[1], q[-sx], q[sx], q[-sy], q[sy], fv, T(0), c);
+    }
+    __syncthreads();
   }
 }
 
@@ -171,16 +263,19 @@ int tasks_at_level(const stencil_ctx* ctx, const TileGeom& tg, int L) {
   return n;
 }
 
-// Site tables of the tile-local levels ii+jj+kk-s for ns = 1..nt, cached per (W, H, D, nt).
+// Site tables of the tile-local levels ii+jj+kk-s for ns = 1..nt, cached per
+// (W, H, D, nt).  Layout in the slot: coords (u32) | lis (u16) | off (int) | base (int).
 static int ensure_sites(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
   if (ctx->gs_key[3] == tg.W && ctx->gs_key[4] == tg.H && ctx->gs_key[5] == tg.D && ctx->gs_key[6] == tg.nt &&
       ctx->slots[SLOT_GS_SITES].ptr)
     return STENCIL_OK;
   std::vector<uint32_t> sites;
+  std::vector<uint16_t> lis;
   std::vector<int> off;
   std::vector<int> base(tg.nt + 1, 0);
   for (int ns = 1; ns <= tg.nt; ++ns) {
     base[ns] = (int)off.size();
+    const int bw = tg.W + ns + 1, bh = tg.H + ns + 1;
     const int lo = -(ns - 1), hi = tg.W + tg.H + tg.D - 3;
     for (int lv = lo; lv <= hi; ++lv) {
       off.push_back((int)sites.size());
@@ -188,20 +283,25 @@ static int ensure_sites(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
         for (int kk = 0; kk < tg.D; ++kk)
           for (int jj = 0; jj < tg.H; ++jj) {
             int ii = lv + s - kk - jj;
-            if (ii >= 0 && ii < tg.W) sites.push_back(pack_site(ii, jj, kk, s));
+            if (ii < 0 || ii >= tg.W) continue;
+            sites.push_back(pack_site(ii, jj, kk, s));
+            lis.push_back((uint16_t)(((kk + ns - s) * bh + (jj + ns - s)) * bw + (ii + ns - s)));
           }
     }
     off.push_back((int)sites.size());
   }
   const size_t b_sites = sites.size() * sizeof(uint32_t);
+  const size_t b_lis = (lis.size() * sizeof(uint16_t) + 15) / 16 * 16;
   const size_t b_off = off.size() * sizeof(int);
   const size_t b_base = base.size() * sizeof(int);
   int status;
-  unsigned char* d = (unsigned char*)ws_get(ctx, SLOT_GS_SITES, b_sites + b_off + b_base + 64, &status);
+  unsigned char* d = (unsigned char*)ws_get(ctx, SLOT_GS_SITES, b_sites + b_lis + b_off + b_base + 64, &status);
   if (!d) return status;
   cudaError_t e = cudaMemcpyAsync(d, sites.data(), b_sites, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d + b_sites, off.data(), b_off, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d + b_sites + b_off, base.data(), b_base, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + b_sites, lis.data(), lis.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + b_sites + b_lis, off.data(), b_off, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d + b_sites + b_lis + b_off, base.data(), b_base, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "upload of site table");
   ctx->gs_key[3] = tg.W; ctx->gs_key[4] = tg.H; ctx->gs_key[5] = tg.D; ctx->gs_key[6] = tg.nt;
@@ -209,27 +309,41 @@ static int ensure_sites(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
   return STENCIL_OK;
 }
 
-template <typename T, class Ar, bool HAS_F, int W, int H, int D>
-static int gs_levels(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, const TileGeom& tg,
-                     cudaStream_t st) {
-  const size_t smem = (size_t)(W + tg.nt + 1) * (H + tg.nt + 1) * (D + tg.nt + 1) * sizeof(T);
-  auto kern = gs_task_kernel<T, Ar, HAS_F, W, H, D>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_err(ctx, e, "gs smem attribute");
+static SiteTable site_table(stencil_ctx* ctx, const TileGeom& tg) {
   const unsigned char* sb = (const unsigned char*)ctx->slots[SLOT_GS_SITES].ptr;
   const size_t nsites = (size_t)ctx->gs_key[7];
-  const uint32_t* sites = (const uint32_t*)sb;
-  const int* site_off = (const int*)(sb + nsites * sizeof(uint32_t));
-  // off has one entry per level per ns plus one terminator per ns
+  const size_t b_sites = nsites * sizeof(uint32_t);
+  const size_t b_lis = (nsites * sizeof(uint16_t) + 15) / 16 * 16;
   size_t noff = 0;
-  for (int ns = 1; ns <= tg.nt; ++ns) noff += (size_t)(W + H + D - 2 + ns - 1) + 1;
-  const int* site_base = site_off + noff;
+  for (int ns = 1; ns <= tg.nt; ++ns) noff += (size_t)(tg.W + tg.H + tg.D - 2 + ns);
+  SiteTable t;
+  t.coords = (const uint32_t*)sb;
+  t.lis = (const uint16_t*)(sb + b_sites);
+  t.off = (const int*)(sb + b_sites + b_lis);
+  t.base = t.off + noff;
+  return t;
+}
+
+template <typename T, class Ar, bool HAS_F, int W, int H, int D>
+static int gs_levels(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, const TileGeom& tg,
+                     bool direct, cudaStream_t st) {
+  size_t smem = (size_t)(W + tg.nt + 1) * (H + tg.nt + 1) * (D + tg.nt + 1) * sizeof(T);
+  auto kern = gs_task_kernel<T, Ar, HAS_F, W, H, D>;
+  cudaError_t e = cudaSuccess;
+  if (direct) {
+    kern = gs_direct_kernel<T, Ar, HAS_F, W, H, D>;
+    smem = 0;
+  } else {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (e != cudaSuccess) return cuda_err(ctx, e, "gs smem attribute");
+  const SiteTable tb = site_table(ctx, tg);
   const uint64_t* slices = slices_ptr(ctx);
   const int* soff = slice_off_ptr(ctx);
   for (int L = 0; L < tg.nlevels; ++L) {
     int n = tasks_at_level(ctx, tg, L);
     if (n == 0) continue;
-    kern<<<n, GS_THREADS, smem, st>>>(u, f, g, c, slices, soff, sites, site_off, site_base, tg, L);
+    kern<<<n, GS_THREADS, smem, st>>>(u, f, g, c, slices, soff, tb, tg, L);
     ctx->launches++;
   }
   e = cudaGetLastError();
@@ -246,6 +360,10 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
   const int ty = (p && p->tile_y) ? p->tile_y : 16;
   const int tz = (p && p->tile_z) ? p->tile_z : 16;
   const int maxnt = sizeof(T) == 8 ? 8 : 16;
+  // variant: in place through L1 (default) or the staged shared-memory box
+  const int variant = p ? p->variant : 0;
+  if (variant < 0 || variant > 2) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
+  const bool direct = variant != 1;
   if (nt > maxnt) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Gauss-Seidel nt = %d > %d for this dtype", nt, maxnt);
   Coef<T> c;
   c.a = T(0);
@@ -259,8 +377,8 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
     tg = make_tile_geom(g, WW, HH, DD, nt, nsweeps);                                     \
     if ((rc = ensure_slices(ctx, tg, st)) != STENCIL_OK) return rc;                      \
     if ((rc = ensure_sites(ctx, tg, st)) != STENCIL_OK) return rc;                       \
-    return f ? gs_levels<T, Ar, true, WW, HH, DD>(ctx, u, f, g, c, tg, st)               \
-             : gs_levels<T, Ar, false, WW, HH, DD>(ctx, u, f, g, c, tg, st);             \
+    return f ? gs_levels<T, Ar, true, WW, HH, DD>(ctx, u, f, g, c, tg, direct, st)       \
+             : gs_levels<T, Ar, false, WW, HH, DD>(ctx, u, f, g, c, tg, direct, st);     \
   }
   GS_TILE(16, 16, 16)
   GS_TILE(8, 8, 8)

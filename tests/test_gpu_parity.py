@@ -103,18 +103,21 @@ def test_gs_f64_ragged(ctx, dims, nsweeps):
 
 @pytest.mark.parametrize("tile", [(16, 16, 16), (8, 8, 8), (32, 8, 8), (32, 16, 16)])
 @pytest.mark.parametrize("nt", [1, 2, 3, 4])
-def test_gs_f64_tiles_temporal(ctx, tile, nt):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_gs_f64_tiles_temporal(ctx, tile, nt, variant):
     u0, f0 = W.random_grid(45, 38, 29, seed=nt, with_f=True)
     ns = 2 * nt + 1
-    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.07, ns, nt=nt, tile=tile), oracle.gs_lex(u0, f0, 0.07, ns),
-                  "gs %s nt=%d" % (tile, nt))
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.07, ns, nt=nt, tile=tile, variant=variant),
+                  oracle.gs_lex(u0, f0, 0.07, ns), "gs %s nt=%d variant %d" % (tile, nt, variant))
 
 
 @pytest.mark.parametrize("nt", [1, 4, 8])
-def test_gs_f32_temporal(ctx, nt):
+@pytest.mark.parametrize("variant", [1, 2])
+def test_gs_f32_temporal(ctx, nt, variant):
     u0, f0 = W.random_grid(40, 33, 27, seed=9, dtype=np.float32, with_f=True)
     ns = 2 * nt + 3
-    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.03, ns, nt=nt), oracle.gs_lex(u0, f0, 0.03, ns), "gs f32")
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.03, ns, nt=nt, variant=variant),
+                  oracle.gs_lex(u0, f0, 0.03, ns), "gs f32")
 
 
 def test_gs_laplace_config1(ctx):
