@@ -47,21 +47,8 @@ __global__ void __launch_bounds__(GS_THREADS) gs_task_kernel(T* __restrict__ u, 
   __shared__ int s_off[GS_MAXLEVELS + 1];
   const int tid = threadIdx.x;
 
-  // ---- which task: blocks of this level enumerate the passes' slices in order
-  int b = blockIdx.x;
-  int p = level / tg.cstride;
-  if (p > tg.npass - 1) p = tg.npass - 1;
-  int sigma = level - tg.cstride * p;
-  for (;;) {
-    int cnt = (sigma <= tg.sigma_max) ? slice_off[sigma + 1] - slice_off[sigma] : 0;
-    if (b < cnt) break;
-    b -= cnt;
-    --p;
-    sigma += tg.cstride;
-    if (p < 0) return;  // cannot happen for a correct launch size
-  }
-  int I, J, K;
-  unpack_tile(slices[slice_off[sigma] + b], &I, &J, &K);
+  int I, J, K, p;
+  if (!find_task(tg, slices, slice_off, level, &I, &J, &K, &p)) return;
   const int ns = min(tg.nt, tg.nsweeps - p * tg.nt);
   const int X0 = I * W, Y0 = J * H, Z0 = K * D;
 
@@ -156,20 +143,8 @@ __global__ void __launch_bounds__(GS_THREADS) gs_direct_kernel(T* u, const T* __
                                                                 TileGeom tg, int level) {
   __shared__ int s_off[GS_MAXLEVELS + 1];
   const int tid = threadIdx.x;
-  int b = blockIdx.x;
-  int p = level / tg.cstride;
-  if (p > tg.npass - 1) p = tg.npass - 1;
-  int sigma = level - tg.cstride * p;
-  for (;;) {
-    int cnt = (sigma <= tg.sigma_max) ? slice_off[sigma + 1] - slice_off[sigma] : 0;
-    if (b < cnt) break;
-    b -= cnt;
-    --p;
-    sigma += tg.cstride;
-    if (p < 0) return;
-  }
-  int I, J, K;
-  unpack_tile(slices[slice_off[sigma] + b], &I, &J, &K);
+  int I, J, K, p;
+  if (!find_task(tg, slices, slice_off, level, &I, &J, &K, &p)) return;
   const int ns = min(tg.nt, tg.nsweeps - p * tg.nt);
   const int X0 = I * W, Y0 = J * H, Z0 = K * D;
   const int nlv = W + H + D - 3 + ns;
@@ -246,8 +221,8 @@ int ensure_slices(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
   return STENCIL_OK;
 }
 
-static const uint64_t* slices_ptr(stencil_ctx* ctx) { return (const uint64_t*)ctx->slots[SLOT_GS_SLICES].ptr; }
-static const int* slice_off_ptr(stencil_ctx* ctx) {
+const uint64_t* slices_ptr(stencil_ctx* ctx) { return (const uint64_t*)ctx->slots[SLOT_GS_SLICES].ptr; }
+const int* slice_off_ptr(stencil_ctx* ctx) {
   size_t ntiles = (size_t)ctx->gs_slice_off.back();
   return (const int*)((const unsigned char*)ctx->slots[SLOT_GS_SLICES].ptr + ntiles * sizeof(uint64_t));
 }
@@ -365,6 +340,9 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
   if (variant < 0 || variant > 2) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
   const bool direct = variant != 1;
   if (nt > maxnt) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Gauss-Seidel nt = %d > %d for this dtype", nt, maxnt);
+  if (nt > tx || nt > ty || nt > tz)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "nt = %d needs every tile extent >= nt (tile %dx%dx%d)", nt, tx, ty,
+                   tz);
   Coef<T> c;
   c.a = T(0);
   c.b = (T)((p && p->b != 0.0) ? p->b : 1.0 / 6.0);

@@ -12,9 +12,14 @@
 // boundary treatment").  Tasks are ordered by the level
 //     L = I + J + K + c*p,  c = 2 if nt == 1, else 4,
 // and all tasks of one level are independent.  Tile counts cover the shifted
-// tiles: NI = ceil((nx + nt - 1) / W).
+// tiles: NI = ceil((nx + nt - 1) / W).  The shift of a pass (nt - 1 cells)
+// must stay below every tile extent, nt <= min(W, H, D): then a task's box
+// meets only tiles one step away and tasks of one level never touch the same
+// site (with nt = min + 1 the result already depends on the order of the
+// tasks within a level).
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace stn {
@@ -44,4 +49,38 @@ __host__ __device__ inline uint32_t pack_site(int ii, int jj, int kk, int s) {
   return (uint32_t)ii | ((uint32_t)jj << 8) | ((uint32_t)kk << 16) | ((uint32_t)s << 24);
 }
 
+}  // namespace stn
+
+struct stencil_ctx;
+namespace stn {
+struct Geom;
+// host helpers (gs.cu): task geometry, the (I,J,K)-by-sigma slice table cached
+// in the context, and the number of tasks of one level
+TileGeom make_tile_geom(const Geom& g, int W, int H, int D, int nt, int nsweeps);
+int ensure_slices(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st);
+int tasks_at_level(const stencil_ctx* ctx, const TileGeom& tg, int L);
+const uint64_t* slices_ptr(stencil_ctx* ctx);
+const int* slice_off_ptr(stencil_ctx* ctx);
+
+// Device: the task (I, J, K, p) that CTA `blockIdx.x` of level `level` runs;
+// false if the index is beyond the level (not for a correctly sized launch).
+__device__ __forceinline__ bool find_task(const TileGeom& tg, const uint64_t* __restrict__ slices,
+                                          const int* __restrict__ slice_off, int level, int* I, int* J, int* K,
+                                          int* p) {
+  int b = blockIdx.x;
+  int pp = level / tg.cstride;
+  if (pp > tg.npass - 1) pp = tg.npass - 1;
+  int sigma = level - tg.cstride * pp;
+  for (;;) {
+    int cnt = (sigma <= tg.sigma_max) ? slice_off[sigma + 1] - slice_off[sigma] : 0;
+    if (b < cnt) break;
+    b -= cnt;
+    --pp;
+    sigma += tg.cstride;
+    if (pp < 0) return false;
+  }
+  unpack_tile(slices[slice_off[sigma] + b], I, J, K);
+  *p = pp;
+  return true;
+}
 }  // namespace stn

@@ -205,3 +205,41 @@ def jacobi_wavefront_paper(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int =
                 else:
                     src[z, J, I] = val
     return src
+
+
+def jacobi_skewed_tiles(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int = 1, tile=(4, 4, 4),
+                        nt: int = 1, reverse_within_level: bool = False) -> np.ndarray:
+    """Jacobi by skewed tiles: the tasks and levels of skewed_tile_tasks, with two
+    arrays holding alternate time levels (level v in array v % 2).  Inside a task
+    the pass-local sweeps s = 0..ns-1 run one after the other, each over the
+    whole shifted tile.  A tile's last column at level v+1 never overwrites the
+    level-v value its forward neighbour still needs, because the skew moves
+    that column out of the tile, so the two arrays alone carry every time level
+    a neighbouring task reads (no boundary copies, no recomputation)."""
+    nz, ny, nx = (s - 2 for s in u.shape)
+    b, hh = _consts(u, h)
+    arr = [u.copy(), u.copy()]  # both carry the halo; level 0 in arr[0]
+    if nsweeps == 0 or nx * ny * nz == 0:
+        return arr[0]
+    W, H, D = tile
+    tasks, _ = skewed_tile_tasks(nx, ny, nz, tile, nt, nsweeps)
+    if reverse_within_level:
+        levels = {}
+        for t in tasks:
+            levels.setdefault(t[0] + t[1] + t[2] + pass_stride(nt) * t[3], []).append(t)
+        tasks = [t for L in sorted(levels) for t in reversed(levels[L])]
+    kk_, jj_, ii_ = np.meshgrid(np.arange(D), np.arange(H), np.arange(W), indexing="ij")
+    kk_, jj_, ii_ = kk_.ravel(), jj_.ravel(), ii_.ravel()
+    for (I, J, K, p) in tasks:
+        ns = min(nt, nsweeps - p * nt)
+        X0, Y0, Z0 = I * W, J * H, K * D
+        for s in range(ns):
+            v = p * nt + s  # level read; level v+1 written
+            x = X0 - s + ii_
+            y = Y0 - s + jj_
+            z = Z0 - s + kk_
+            ok = (x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0) & (z < nz)
+            k, j, i = z[ok], y[ok], x[ok]
+            if k.size:
+                arr[(v + 1) % 2][k + 1, j + 1, i + 1] = _update(arr[v % 2], f, k, j, i, b, hh)
+    return arr[nsweeps % 2]

@@ -85,6 +85,33 @@ def test_jacobi_f32_bit_exact(ctx, dims):
     _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.02, 3), oracle.jacobi(u0, f0, 0.02, 3), "jacobi f32")
 
 
+@pytest.mark.parametrize("tile", [(32, 8, 8), (32, 16, 8), (32, 16, 16), (16, 16, 16), (64, 8, 8)])
+@pytest.mark.parametrize("nt", [2, 3, 4, 8])
+def test_jacobi_temporal_f64(ctx, tile, nt):
+    """Temporal blocking (nt sweeps per pass on skewed tiles): bit-exact, odd and even counts."""
+    u0, f0 = W.random_grid(45, 38, 29, seed=nt, with_f=True)
+    for ns in (nt, 2 * nt + 1):
+        _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.07, ns, nt=nt, tile=tile),
+                      oracle.jacobi(u0, f0, 0.07, ns), "jacobi %s nt=%d ns=%d" % (tile, nt, ns))
+
+
+@pytest.mark.parametrize("nt", [2, 4, 8, 16])
+def test_jacobi_temporal_f32_and_weighted(ctx, nt):
+    u0, f0 = W.random_grid(40, 33, 27, seed=9, dtype=np.float32, with_f=True)
+    ns = 2 * nt + 3
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.03, ns, nt=nt), oracle.jacobi(u0, f0, 0.03, ns), "f32")
+    u1, f1 = W.random_grid(21, 17, 13, seed=2, with_f=True)
+    a, b = 0.2, 0.8 / 6.0
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u1, f1, 0.1, ns, nt=nt, a=a, b=b),
+                  oracle.jacobi(u1, f1, 0.1, ns, a=a, b=b), "weighted temporal")
+
+
+@pytest.mark.parametrize("dims", RAGGED)
+def test_jacobi_temporal_ragged(ctx, dims):
+    u0, f0 = W.random_grid(*dims, seed=5, with_f=True)
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.3, 7, nt=4), oracle.jacobi(u0, f0, 0.3, 7), str(dims))
+
+
 def test_jacobi_zero_sweeps_and_empty(ctx):
     u0, _ = W.random_grid(7, 6, 5, seed=1)
     _assert_exact(_run(ctx, capi.stencil_jacobi, u0, None, 1.0, 0), u0, "zero sweeps")
@@ -184,6 +211,9 @@ def test_argument_errors(ctx):
     with pytest.raises(capi.StencilError) as e:
         capi.stencil_jacobi(ctx, u, None, 1.0, 1, nt=17)
     assert e.value.code == capi.STENCIL_ERR_ARG
+    with pytest.raises(capi.StencilError) as e:
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 1, nt=9, tile=(8, 8, 8))
+    assert e.value.code == capi.STENCIL_ERR_UNSUPPORTED
 
 
 def test_budget_oom():

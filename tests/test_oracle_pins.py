@@ -140,7 +140,8 @@ def test_gs_hyperplane_order_is_bit_exact(dims):
 
 
 @pytest.mark.parametrize("tile,nt", [((4, 4, 4), 1), ((3, 2, 4), 1), ((4, 4, 4), 2), ((4, 3, 5), 3),
-                                     ((8, 4, 2), 2), ((2, 2, 2), 2), ((5, 5, 5), 4)])
+                                     ((8, 4, 2), 2), ((2, 2, 2), 2), ((5, 5, 5), 4), ((3, 3, 3), 3),
+                                     ((4, 4, 4), 4)])
 @pytest.mark.parametrize("reverse", [False, True])
 def test_gs_skewed_tiles_are_bit_exact(tile, nt, reverse):
     """The skewed-tile schedule (nt sweeps per task, tasks by level I+J+K+c*p)
@@ -311,3 +312,32 @@ def test_f32_gs_is_lower_triangular_solve():
     ref = spla.spsolve_triangular(m, U @ F.interior(u64) + F.boundary_sum(u64) + (h * h) * F.interior(f64), lower=True)
     out = oracle.gs_lex(u, f, h, 1)
     np.testing.assert_allclose(F.interior(out), ref, rtol=64 * EPS32, atol=64 * EPS32)
+
+
+@pytest.mark.parametrize("tile,nt", [((4, 4, 4), 1), ((4, 4, 4), 2), ((4, 3, 5), 3), ((8, 4, 2), 2),
+                                     ((2, 2, 2), 2), ((5, 5, 5), 4), ((3, 3, 3), 3), ((4, 4, 4), 4)])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_jacobi_skewed_tiles_are_bit_exact(tile, nt, reverse):
+    """Jacobi on the same skewed-tile schedule with two parity arrays equals the
+    plain two-array sweeps (temporal blocking without extra computation, Sec. 4)."""
+    nx, ny, nz = 9, 7, 8
+    rng = np.random.default_rng(6)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    for nsweeps in (1, nt, 2 * nt + 1):
+        ref = oracle.jacobi(u, f, 0.2, nsweeps)
+        out = S.jacobi_skewed_tiles(u, f, 0.2, nsweeps, tile, nt, reverse)
+        assert np.array_equal(out, ref), (tile, nt, nsweeps)
+
+
+def test_skewed_tiles_depth_limit_is_sharp():
+    """nt <= min(tile) is needed: with nt = min + 1 the result depends on the
+    order of tasks within one level (tasks of a level then share sites)."""
+    nx, ny, nz = 9, 7, 8
+    rng = np.random.default_rng(6)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    ns = 9
+    ref_g, ref_j = oracle.gs_lex(u, f, 0.2, ns), oracle.jacobi(u, f, 0.2, ns)
+    assert not np.array_equal(S.gs_skewed_tiles(u, f, 0.2, ns, (3, 3, 3), 4, True), ref_g)
+    assert not np.array_equal(S.jacobi_skewed_tiles(u, f, 0.2, ns, (3, 3, 3), 4, True), ref_j)
