@@ -151,6 +151,27 @@ int stencil_gs_lex_f32(stencil_ctx* ctx, float* u, const float* f, const int64_t
 int residual_norm(stencil_ctx* ctx, const double* u, const double* f, const int64_t dims[3], double h,
                   double* r_out, double* out_abs, double* out_rel, void* stream);
 
+/* residual_norm without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc when they
+ * need a residual (an application that owns all device memory through its
+ * own allocator, a time-critical loop that must not stall or fragment the
+ * heap, code about to be recorded into a CUDA graph).  Same arguments,
+ * results and reduction order as residual_norm, but no context: the work
+ * runs on the calling thread's current CUDA device, and u, f, r_out must
+ * live there.  The reduction scratch is a fixed array inside the library
+ * (512 KiB + 16 B on every device that loads it, held until the process
+ * exits), so the grid must satisfy
+ *     ceil(nx/32) * ceil(ny/8) * ceil(nz/32) <= 32768
+ * (e.g. up to 640^3); larger grids return STENCIL_ERR_ARG with the limit in
+ * stencil_last_error(NULL).  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  Every
+ * call reuses the same array: calls that overlap on the GPU (two streams,
+ * two host threads on one device) race and must be serialised by the
+ * caller.  Blocking: synchronises `stream`.  Errors are reported through
+ * stencil_last_error(NULL). */
+int residual_norm_noalloc(const double* u, const double* f, const int64_t dims[3], double h, double* r_out,
+                          double* out_abs, double* out_rel, void* stream);
+
 /* Mixed-precision Poisson solve by defect correction (not in the paper):
  *   repeat: r = f - A u (FP64); e = 0; inner_sweeps FP32 sweeps of
  *   `smoother` (STENCIL_JACOBI or STENCIL_GS) on A e = (float) r;

@@ -68,6 +68,7 @@ _SIGS = {
     "stencil_gs_lex_ex": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
     "stencil_gs_lex_f32": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
     "residual_norm": (_I, [_P, _P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
+    "residual_norm_noalloc": (_I, [_P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stencil_solve_mixed": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
     "stencil_solve_f64": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, _PP, ctypes.POINTER(_D), ctypes.POINTER(_I),
                                _P]),
@@ -223,6 +224,20 @@ def residual_norm(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: floa
     rc = lib.residual_norm(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u), float(h),
                            _opt_grid(r_out, u, torch.float64), ctypes.byref(ab), ctypes.byref(rel), _stream(stream))
     _check(ctx, rc)
+    return ab.value, rel.value
+
+
+def residual_norm_noalloc(u: torch.Tensor, f: torch.Tensor | None, h: float, r_out: torch.Tensor | None = None,
+                          stream=None):
+    """residual_norm for callers that cannot allocate device memory: no context,
+    a fixed scratch array inside the library, the current CUDA device.  Returns
+    (||r||_2, ||r||_2/||f||_2)."""
+    lib = load_library()
+    ab, rel = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib.residual_norm_noalloc(_grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u), float(h),
+                                   _opt_grid(r_out, u, torch.float64), ctypes.byref(ab), ctypes.byref(rel),
+                                   _stream(stream))
+    _check(None, rc)
     return ab.value, rel.value
 
 
