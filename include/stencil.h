@@ -102,8 +102,10 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          else STENCIL_ERR_UNSUPPORTED.
  *  a, b    weights of the site update; b == 0 means 1/6.  a != 0 is only
  *          accepted by Jacobi (weighted Jacobi, a = 1 - omega, b = omega/6).
- *  variant kernel variant (Gauss-Seidel): 0 = default, 1 = tile staged in
- *          shared memory, 2 = tile updated in place through the L1 cache.
+ *  variant kernel variant: 0 = default; Gauss-Seidel 1 = tile staged in
+ *          shared memory, 2 = tile updated in place through the L1 cache
+ *          (one launch per tile level); 3 (both smoothers) = one persistent
+ *          dataflow launch over a dependency-ordered task queue (blocking).
  *          Every variant gives the same bits. */
 typedef struct stencil_params {
   int nt;
@@ -150,6 +152,37 @@ int stencil_gs_lex_f32(stencil_ctx* ctx, float* u, const float* f, const int64_t
  * order for a given dims, so repeated calls give identical bits. */
 int residual_norm(stencil_ctx* ctx, const double* u, const double* f, const int64_t dims[3], double h,
                   double* r_out, double* out_abs, double* out_rel, void* stream);
+
+/* Batched smoothing of n independent grids of uneven sizes in ONE persistent
+ * kernel launch, replayed from a CUDA graph (not in the paper; the tile tasks
+ * of all grids share one dependency-ordered work queue, so small grids fill
+ * the GPU together).  u[i], f[i]: device pointers of grid i (f may be NULL,
+ * or f[i] NULL, for f = 0); dims[3i..3i+2] its interior extents; h[i],
+ * nsweeps[i] (host arrays).  smoother: STENCIL_JACOBI or STENCIL_GS; dtype:
+ * STENCIL_F64 or STENCIL_F32 (u and f are double* or float* accordingly).
+ * Every grid ends exactly as after stencil_jacobi / stencil_gs_lex with the
+ * same arguments.  params (may be NULL): nt and tile shared by all grids
+ * (defaults: GS 16^3, Jacobi 32x8x8, nt = 1); a must be 0.  Jacobi takes a
+ * workspace of the total size of the batch.  Blocking: returns when the batch
+ * is done; STENCIL_ERR_TIMEOUT if a bounded device wait expired (the grids
+ * are then undefined, the context stays usable). */
+int stencil_batched(stencil_ctx* ctx, int n, void* const* u, const void* const* f, const int64_t* dims,
+                    const double* h, const int* nsweeps, int smoother, int dtype, const stencil_params* params,
+                    void* stream);
+
+/* Bound on every device-side wait of the persistent kernels (default 10 s).
+ * never_publish >= 0 makes the task at that queue index never publish its
+ * completion, so that a test can watch the bound expire and the error come
+ * back (STENCIL_ERR_TIMEOUT); pass -1 for normal operation. */
+int stencil_set_wait_limit(stencil_ctx* ctx, long long timeout_ns, long long never_publish);
+
+/* Autotuner (not in the paper): times candidate kernel variants, temporal
+ * depths nt and tiles for `smoother` on a copy of the caller's grid u (device,
+ * dtype STENCIL_F64/F32; f may be NULL) for nsweeps sweeps and writes the
+ * fastest into *out (and its GLUP/s into *out_glups if not NULL).  u is not
+ * modified.  Blocking. */
+int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, const void* f, const int64_t dims[3],
+                     double h, int nsweeps, stencil_params* out, double* out_glups, void* stream);
 
 /* residual_norm without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc when they

@@ -68,6 +68,10 @@ _SIGS = {
     "stencil_gs_lex_ex": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
     "stencil_gs_lex_f32": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
     "residual_norm": (_I, [_P, _P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
+    "stencil_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I64P, ctypes.POINTER(_D),
+                             ctypes.POINTER(_I), _I, _I, _PP, _P]),
+    "stencil_set_wait_limit": (_I, [_P, ctypes.c_longlong, ctypes.c_longlong]),
+    "stencil_autotune": (_I, [_P, _I, _I, _P, _P, _I64P, _D, _I, _PP, ctypes.POINTER(_D), _P]),
     "residual_norm_noalloc": (_I, [_P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stencil_solve_mixed": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
     "stencil_solve_f64": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, _PP, ctypes.POINTER(_D), ctypes.POINTER(_I),
@@ -189,10 +193,10 @@ class Context:
 
 # ------------------------------------------------------------ entry points --
 def stencil_jacobi(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int, *, nt: int = 0,
-                   tile=(0, 0, 0), a: float = 0.0, b: float = 0.0, stream=None) -> None:
+                   tile=(0, 0, 0), a: float = 0.0, b: float = 0.0, variant: int = 0, stream=None) -> None:
     """Jacobi sweeps in place on u (FP64 or FP32 by u's dtype)."""
     lib = load_library()
-    p = _params(nt, tile, a, b)
+    p = _params(nt, tile, a, b, variant)
     if u.dtype == torch.float64:
         rc = lib.stencil_jacobi_ex(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
                                    float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
@@ -225,6 +229,48 @@ def residual_norm(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: floa
                            _opt_grid(r_out, u, torch.float64), ctypes.byref(ab), ctypes.byref(rel), _stream(stream))
     _check(ctx, rc)
     return ab.value, rel.value
+
+
+def stencil_batched(ctx: Context, us, fs, hs, nsweeps, smoother: int, *, nt: int = 0, tile=(0, 0, 0),
+                    stream=None) -> None:
+    """Smooth many grids (a list of tensors, one dtype) in one persistent launch."""
+    lib = load_library()
+    n = len(us)
+    if n == 0:
+        return
+    dt = us[0].dtype
+    dtype = STENCIL_F64 if dt == torch.float64 else STENCIL_F32
+    up = (ctypes.c_void_p * n)(*[_grid(u, dt).value for u in us])
+    fp = None
+    if fs is not None:
+        fp = (ctypes.c_void_p * n)(*[(_opt_grid(f, u, dt).value if f is not None else None) for f, u in zip(fs, us)])
+    dims = (ctypes.c_int64 * (3 * n))()
+    for i, u in enumerate(us):
+        d = _dims(u)
+        dims[3 * i], dims[3 * i + 1], dims[3 * i + 2] = d[0], d[1], d[2]
+    hh = (ctypes.c_double * n)(*[float(x) for x in hs])
+    ns = (ctypes.c_int * n)(*[int(x) for x in nsweeps])
+    p = _params(nt, tile)
+    rc = lib.stencil_batched(ctx.handle, n, up, fp, dims, hh, ns, int(smoother), dtype, ctypes.byref(p),
+                             _stream(stream))
+    _check(ctx, rc)
+
+
+def stencil_set_wait_limit(ctx: Context, timeout_ns: int, never_publish: int = -1) -> None:
+    _check(ctx, load_library().stencil_set_wait_limit(ctx.handle, int(timeout_ns), int(never_publish)))
+
+
+def stencil_autotune(ctx: Context, smoother: int, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int,
+                     stream=None):
+    """Returns (params dict, GLUP/s) of the fastest candidate on a copy of u."""
+    lib = load_library()
+    out = stencil_params()
+    g = ctypes.c_double(0.0)
+    dtype = STENCIL_F64 if u.dtype == torch.float64 else STENCIL_F32
+    rc = lib.stencil_autotune(ctx.handle, int(smoother), dtype, _grid(u, u.dtype), _opt_grid(f, u, u.dtype), _dims(u),
+                              float(h), int(nsweeps), ctypes.byref(out), ctypes.byref(g), _stream(stream))
+    _check(ctx, rc)
+    return ({"nt": out.nt, "tile": (out.tile_x, out.tile_y, out.tile_z), "variant": out.variant}, g.value)
 
 
 def residual_norm_noalloc(u: torch.Tensor, f: torch.Tensor | None, h: float, r_out: torch.Tensor | None = None,

@@ -1,0 +1,177 @@
+// Batched smoothing of many grids of uneven sizes in one persistent launch
+// (dataflow.cu), and the autotuner that picks tile, nt and kernel variant.
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "tiles.h"
+
+namespace stn {
+
+template <typename T>
+static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* const* f, const int64_t* dims,
+                       const double* h, const int* nsweeps, int smoother, const stencil_params* p, cudaStream_t st) {
+  std::vector<Geom> geoms((size_t)n);
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    int rc = check_dims(ctx, dims + 3 * (size_t)i, &geoms[(size_t)i]);
+    if (rc) return rc;
+    if (!u[i]) return set_err(ctx, STENCIL_ERR_ARG, "u[%d] is NULL", i);
+    if (nsweeps[i] < 0) return set_err(ctx, STENCIL_ERR_ARG, "nsweeps[%d] < 0", i);
+    if (!(h[i] > 0.0) || !std::isfinite(h[i])) return set_err(ctx, STENCIL_ERR_ARG, "h[%d] must be > 0", i);
+    total += (size_t)geoms[(size_t)i].sy * (size_t)(geoms[(size_t)i].nz + 2);
+  }
+  const int nt = (p && p->nt > 0) ? p->nt : 1;
+  const int W = (p && p->tile_x) ? p->tile_x : (smoother == STENCIL_GS ? 16 : 32);
+  const int H = (p && p->tile_y) ? p->tile_y : (smoother == STENCIL_GS ? 16 : 8);
+  const int D = (p && p->tile_z) ? p->tile_z : (smoother == STENCIL_GS ? 16 : 8);
+  if (nt > W || nt > H || nt > D)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "nt = %d needs every tile extent >= nt (tile %dx%dx%d)", nt, W, H, D);
+  if (p && p->a != 0.0) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "weighted sweeps are not batched");
+  std::vector<T*> a((size_t)n), b((size_t)n);
+  std::vector<const T*> fs((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    a[(size_t)i] = (T*)u[i];
+    fs[(size_t)i] = f ? (const T*)f[i] : nullptr;
+  }
+  if (smoother == STENCIL_JACOBI) {
+    int status;
+    T* tmp = (T*)ws_get(ctx, SLOT_BATCH_TMP, total * sizeof(T), &status);
+    if (!tmp) return status;
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+      const size_t cnt = (size_t)geoms[(size_t)i].sy * (size_t)(geoms[(size_t)i].nz + 2);
+      T* ti = tmp + off;
+      off += cnt;
+      cudaError_t e = cudaMemcpyAsync(ti, u[i], cnt * sizeof(T), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_err(ctx, e, "batched halo copy");
+      // level nsweeps must land in u[i]
+      const bool odd = nsweeps[i] % 2;
+      a[(size_t)i] = odd ? ti : (T*)u[i];
+      b[(size_t)i] = odd ? (T*)u[i] : ti;
+    }
+  }
+  return dataflow_run<T>(ctx, smoother, n, a.data(), smoother == STENCIL_JACOBI ? b.data() : nullptr, fs.data(),
+                         geoms.data(), nsweeps, h, W, H, D, nt, ctx->df_timeout_ns, ctx->df_poison, st);
+}
+
+}  // namespace stn
+
+using namespace stn;
+
+extern "C" {
+
+int stencil_batched(stencil_ctx* ctx, int n, void* const* u, const void* const* f, const int64_t* dims,
+                    const double* h, const int* nsweeps, int smoother, int dtype, const stencil_params* params,
+                    void* stream) {
+  if (!ctx) return STENCIL_ERR_ARG;
+  ctx->err.clear();
+  if (n < 0 || (n > 0 && (!u || !dims || !h || !nsweeps))) return set_err(ctx, STENCIL_ERR_ARG, "bad batch arrays");
+  if (n == 0) return STENCIL_OK;
+  if (smoother != STENCIL_JACOBI && smoother != STENCIL_GS) return set_err(ctx, STENCIL_ERR_ARG, "bad smoother");
+  if (params && (params->nt < 0 || params->nt > 16)) return set_err(ctx, STENCIL_ERR_ARG, "nt out of range");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == STENCIL_F64) return batched_run<double>(ctx, n, u, f, dims, h, nsweeps, smoother, params, st);
+  if (dtype == STENCIL_F32) return batched_run<float>(ctx, n, u, f, dims, h, nsweeps, smoother, params, st);
+  return set_err(ctx, STENCIL_ERR_ARG, "bad dtype %d", dtype);
+}
+
+int stencil_set_wait_limit(stencil_ctx* ctx, long long timeout_ns, long long never_publish) {
+  if (!ctx || timeout_ns <= 0) return STENCIL_ERR_ARG;
+  ctx->df_timeout_ns = timeout_ns;
+  ctx->df_poison = never_publish;
+  return STENCIL_OK;
+}
+
+int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, const void* f, const int64_t dims[3],
+                     double h, int nsweeps, stencil_params* out, double* out_glups, void* stream) {
+  if (!ctx) return STENCIL_ERR_ARG;
+  ctx->err.clear();
+  Geom g;
+  int rc = check_dims(ctx, dims, &g);
+  if (rc) return rc;
+  if (!u || !out) return set_err(ctx, STENCIL_ERR_ARG, "u and out are required");
+  if (smoother != STENCIL_JACOBI && smoother != STENCIL_GS) return set_err(ctx, STENCIL_ERR_ARG, "bad smoother");
+  if (dtype != STENCIL_F64 && dtype != STENCIL_F32) return set_err(ctx, STENCIL_ERR_ARG, "bad dtype");
+  if (nsweeps <= 0 || !(h > 0.0)) return set_err(ctx, STENCIL_ERR_ARG, "nsweeps > 0 and h > 0 required");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t esz = dtype == STENCIL_F64 ? 8 : 4;
+  const size_t bytes = (size_t)g.sy * (size_t)(g.nz + 2) * esz;
+  // candidates: (variant, nt, tile); the caller's grid is copied, never modified
+  struct Cand {
+    int variant, nt, tx, ty, tz;
+  };
+  std::vector<Cand> cands;
+  if (smoother == STENCIL_GS) {
+    const int nts[] = {1, 2, 4, 8};
+    const int tiles[][3] = {{16, 16, 16}, {32, 8, 8}, {32, 16, 16}};
+    for (int v : {0, 3})
+      for (int nt : nts)
+        for (auto& t : tiles)
+          if (nt <= t[1] && nt <= t[2] && (dtype == STENCIL_F32 || nt <= 8)) cands.push_back({v, nt, t[0], t[1], t[2]});
+  } else {
+    for (int by : {4, 8, 16}) cands.push_back({0, 1, 32, by, 0});
+    const int nts[] = {2, 4, 8};
+    const int tiles[][3] = {{32, 8, 8}, {32, 16, 8}, {32, 16, 16}};
+    for (int nt : nts)
+      for (auto& t : tiles) cands.push_back({0, nt, t[0], t[1], t[2]});
+  }
+  int status;
+  void* scratch = ws_get(ctx, SLOT_TUNE_GRID, bytes, &status);
+  if (!scratch) return status;
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_err(ctx, e, "cudaEventCreate");
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_err(ctx, e, "cudaEventCreate");
+  }
+  double best = -1.0;
+  Cand bestc = cands[0];
+  for (const Cand& c : cands) {
+    stencil_params q{};
+    q.nt = c.nt;
+    q.tile_x = c.tx;
+    q.tile_y = c.ty;
+    q.tile_z = c.tz;
+    q.variant = c.variant;
+    e = cudaMemcpyAsync(scratch, u, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) break;
+    auto run = [&]() -> int {
+      if (dtype == STENCIL_F64)
+        return smoother == STENCIL_GS ? gs_run<double>(ctx, (double*)scratch, (const double*)f, g, h, nsweeps, &q, st)
+                                      : jacobi_run<double>(ctx, (double*)scratch, (const double*)f, g, h, nsweeps, &q, st);
+      return smoother == STENCIL_GS ? gs_run<float>(ctx, (float*)scratch, (const float*)f, g, h, nsweeps, &q, st)
+                                    : jacobi_run<float>(ctx, (float*)scratch, (const float*)f, g, h, nsweeps, &q, st);
+    };
+    if (run() != STENCIL_OK) continue;  // warm-up (builds tables and plans); skip unsupported shapes
+    cudaEventRecord(e0, st);
+    int r2 = run();
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || r2 != STENCIL_OK) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double glups = (double)g.nx * g.ny * g.nz * nsweeps / (ms * 1e-3) / 1e9;
+    if (glups > best) {
+      best = glups;
+      bestc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return set_err(ctx, STENCIL_ERR_CUDA, "no candidate ran");
+  ctx->err.clear();
+  *out = stencil_params{};
+  out->nt = bestc.nt;
+  out->tile_x = bestc.tx;
+  out->tile_y = bestc.ty;
+  out->tile_z = bestc.tz;
+  out->variant = bestc.variant;
+  if (out_glups) *out_glups = best;
+  return STENCIL_OK;
+}
+
+}  // extern "C"

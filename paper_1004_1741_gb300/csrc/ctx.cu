@@ -132,9 +132,11 @@ void stencil_destroy(stencil_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  dataflow_release(ctx);
   for (auto& s : ctx->slots)
     if (s.ptr) cudaFree(s.ptr);
   if (ctx->ev) cudaEventDestroy(ctx->ev);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
   delete ctx;
 }
 

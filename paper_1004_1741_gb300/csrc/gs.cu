@@ -22,20 +22,9 @@
 
 #include "internal.h"
 #include "tiles.h"
+#include "task_bodies.cuh"
 
 namespace stn {
-
-constexpr int GS_THREADS = 256;
-constexpr int GS_MAXPOS = 8;     // box-plane positions per thread: (W+nt+1)(H+nt+1) <= 8*256
-constexpr int GS_MAXLEVELS = 128;  // tile-local levels W+H+D-3+ns <= 128
-
-// Site table of the tile-local levels (built on the host, see ensure_sites).
-struct SiteTable {
-  const uint32_t* coords;  // packed (ii, jj, kk, s)
-  const uint16_t* lis;     // shared-memory index of the site inside the staged box
-  const int* off;          // level offsets, per ns one block of W+H+D-2+ns entries
-  const int* base;         // base[ns]: first entry of ns's block in off
-};
 
 template <typename T, class Ar, bool HAS_F, int W, int H, int D>
 __global__ void __launch_bounds__(GS_THREADS) gs_task_kernel(T* __restrict__ u, const T* __restrict__ f, Geom g,
@@ -128,51 +117,17 @@ __global__ void __launch_bounds__(GS_THREADS) gs_task_kernel(T* __restrict__ u, 
   }
 }
 
-// Direct variant: the same schedule, but the task updates the grid in place
-// through the L1 cache instead of staging a box in shared memory.  A site
-// written at tile level lv is read at level lv+1 by threads of the same CTA
-// after the barrier (global writes of a CTA are visible to the CTA after
-// __syncthreads); everything written by other tasks comes from earlier
-// launches.  Without a shared-memory box, up to eight CTAs fit on an SM,
-// which keeps enough independent FP64 chains in flight to fill the SM's
-// FP64 pipe.
+// Direct variant (default): the task body of task_bodies.cuh, one CTA per task
+// of the level.
 template <typename T, class Ar, bool HAS_F, int W, int H, int D>
 __global__ void __launch_bounds__(GS_THREADS) gs_direct_kernel(T* u, const T* __restrict__ f, Geom g, Coef<T> c,
                                                                 const uint64_t* __restrict__ slices,
                                                                 const int* __restrict__ slice_off, SiteTable tb,
                                                                 TileGeom tg, int level) {
   __shared__ int s_off[GS_MAXLEVELS + 1];
-  const int tid = threadIdx.x;
   int I, J, K, p;
   if (!find_task(tg, slices, slice_off, level, &I, &J, &K, &p)) return;
-  const int ns = min(tg.nt, tg.nsweeps - p * tg.nt);
-  const int X0 = I * W, Y0 = J * H, Z0 = K * D;
-  const int nlv = W + H + D - 3 + ns;
-  const int* so = tb.off + tb.base[ns];
-  for (int l = tid; l <= nlv; l += GS_THREADS) s_off[l] = so[l];
-  const bool full = (X0 - ns + 1 >= 0) && (Y0 - ns + 1 >= 0) && (Z0 - ns + 1 >= 0) && (X0 + W <= g.nx) &&
-                    (Y0 + H <= g.ny) && (Z0 + D <= g.nz);
-  const int64_t sx = g.sx, sy = g.sy;
-  T* ut = u + g.at(X0, Y0, Z0);  // site (ii, jj, kk) of sweep s at ut[(kk-s)*sy + (jj-s)*sx + (ii-s)]
-  __syncthreads();
-  for (int lv = 0; lv < nlv; ++lv) {
-    const int beg = s_off[lv], end = s_off[lv + 1];
-    int t = tid - (((int)blockIdx.x + lv) & 7) * 32;
-    if (t < 0) t += GS_THREADS;
-    for (int e = beg + t; e < end; e += GS_THREADS) {
-      const uint32_t s = tb.coords[e];
-      const int sw = (int)(s >> 24);
-      const int dx = (int)(s & 0xFF) - sw, dy = (int)((s >> 8) & 0xFF) - sw, dz = (int)((s >> 16) & 0xFF) - sw;
-      if (!full && (X0 + dx < 0 || X0 + dx >= g.nx || Y0 + dy < 0 || Y0 + dy >= g.ny || Z0 + dz < 0 ||
-                    Z0 + dz >= g.nz))
-        continue;
-      T* q = ut + ((int64_t)dz * sy + (int64_t)dy * sx + dx);
-      T fv = T(0);
-      if (HAS_F) fv = f[q - u];
-      *q = site_update<T, Ar, HAS_F, false>(q[-1], q[1], q[-sx], q[sx], q[-sy], q[sy], fv, T(0), c);
-    }
-    __syncthreads();
-  }
+  gs_task_body<T, Ar, HAS_F, W, H, D>(u, f, g, c, tb, tg, I, J, K, p, s_off);
 }
 
 // ---------------------------------------------------------------------------
@@ -240,7 +195,7 @@ int tasks_at_level(const stencil_ctx* ctx, const TileGeom& tg, int L) {
 
 // Site tables of the tile-local levels ii+jj+kk-s for ns = 1..nt, cached per
 // (W, H, D, nt).  Layout in the slot: coords (u32) | lis (u16) | off (int) | base (int).
-static int ensure_sites(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
+int ensure_sites(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
   if (ctx->gs_key[3] == tg.W && ctx->gs_key[4] == tg.H && ctx->gs_key[5] == tg.D && ctx->gs_key[6] == tg.nt &&
       ctx->slots[SLOT_GS_SITES].ptr)
     return STENCIL_OK;
@@ -284,7 +239,7 @@ static int ensure_sites(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
   return STENCIL_OK;
 }
 
-static SiteTable site_table(stencil_ctx* ctx, const TileGeom& tg) {
+SiteTable site_table(stencil_ctx* ctx, const TileGeom& tg) {
   const unsigned char* sb = (const unsigned char*)ctx->slots[SLOT_GS_SITES].ptr;
   const size_t nsites = (size_t)ctx->gs_key[7];
   const size_t b_sites = nsites * sizeof(uint32_t);
@@ -337,8 +292,16 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
   const int maxnt = sizeof(T) == 8 ? 8 : 16;
   // variant: in place through L1 (default) or the staged shared-memory box
   const int variant = p ? p->variant : 0;
-  if (variant < 0 || variant > 2) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
+  if (variant < 0 || variant > 3) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
   const bool direct = variant != 1;
+  if (variant == 3) {
+    T* const a[1] = {u};
+    const T* const fs[1] = {f};
+    const int ns[1] = {nsweeps};
+    const double hs[1] = {h};
+    return dataflow_run<T>(ctx, STENCIL_GS, 1, a, nullptr, fs, &g, ns, hs, tx, ty, tz, nt, ctx->df_timeout_ns,
+                           ctx->df_poison, st);
+  }
   if (nt > maxnt) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Gauss-Seidel nt = %d > %d for this dtype", nt, maxnt);
   if (nt > tx || nt > ty || nt > tz)
     return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "nt = %d needs every tile extent >= nt (tile %dx%dx%d)", nt, tx, ty,

@@ -30,6 +30,9 @@ enum SlotId {
   SLOT_GS_SLICES,        // Gauss-Seidel tile slices (I,J,K by I+J+K)
   SLOT_GS_SITES,         // Gauss-Seidel intra-tile site table
   SLOT_BATCH_DESC,       // batched-launch descriptors
+  SLOT_DF_QUEUE,         // dataflow run: grid descriptors, task queue, completion flags
+  SLOT_BATCH_TMP,        // batched Jacobi: second grids
+  SLOT_TUNE_GRID,        // autotuner: copy of the caller's grid
   SLOT_COUNT
 };
 
@@ -46,6 +49,12 @@ struct stencil_ctx {
   std::vector<int> gs_slice_off;  // host copy of the slice prefix offsets
   int sm_count = 0;
   unsigned long long launches = 0;  // kernels this context has launched
+  void* pinned = nullptr;           // small pinned host buffer for status words
+  long long df_timeout_ns = 10000000000LL;  // bound on every dataflow wait
+  long long df_poison = -1;                 // failure tests: queue index never published
+  void* df_plans = nullptr;                 // cached dataflow plans (dataflow.cu)
+  unsigned long long df_clock = 0;
+  cudaStream_t gstream = nullptr;           // stream for graph capture and replay
   cudaEvent_t ev = nullptr;
 };
 
@@ -73,5 +82,14 @@ int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Ge
                     double* r_out, float* r32_out, double** result, cudaStream_t st);
 // u[interior] += (double) e[interior]
 int correct_launch(stencil_ctx* ctx, double* u, const float* e, const Geom& g, cudaStream_t st);
+
+constexpr int STENCIL_UNSUPPORTED_TILE = 1;
+void dataflow_release(stencil_ctx* ctx);  // internal: no kernel instantiated for a tile shape
+
+// Persistent dataflow run of the skewed-tile schedule over n grids (dataflow.cu).
+template <typename T>
+int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, const T* const* f, const Geom* geoms,
+                 const int* nsweeps, const double* h, int W, int H, int D, int nt, long long timeout_ns,
+                 long long poison, cudaStream_t st);
 
 }  // namespace stn

@@ -126,7 +126,11 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   T* tmp = (T*)ws_get(ctx, SLOT_JACOBI_TMP, bytes, &status);
   if (!tmp) return status;
   const int nt = (p && p->nt > 0) ? p->nt : 1;
-  if (nt > 1) return tb_jacobi_run<T>(ctx, u, tmp, f, g, h, nsweeps, p, st);
+  if (nt > 1 || (p && p->variant == 3)) {
+    stencil_params q = *p;
+    q.nt = nt;
+    return tb_jacobi_run<T>(ctx, u, tmp, f, g, h, nsweeps, &q, st);
+  }
   const bool weighted = p && p->a != 0.0;
   Coef<T> c = make_coef<T>(h, p);
   int by = (p && p->tile_y) ? p->tile_y : 8;

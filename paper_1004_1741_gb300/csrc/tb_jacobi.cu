@@ -14,10 +14,11 @@
 // of level p*nt and its single write of level (p+1)*nt.
 #include "internal.h"
 #include "tiles.h"
+#include "task_bodies.cuh"
 
 namespace stn {
 
-constexpr int TBJ_THREADS = 256;
+constexpr int TBJ_THREADS = GS_THREADS;
 
 template <typename T, class Ar, bool HAS_F, bool WEIGHTED, int W, int H, int D>
 __global__ void __launch_bounds__(TBJ_THREADS) jacobi_task_kernel(T* g_even, T* g_odd, const T* __restrict__ f,
@@ -27,33 +28,7 @@ __global__ void __launch_bounds__(TBJ_THREADS) jacobi_task_kernel(T* g_even, T* 
                                                                    int level) {
   int I, J, K, p;
   if (!find_task(tg, slices, slice_off, level, &I, &J, &K, &p)) return;
-  const int ns = min(tg.nt, tg.nsweeps - p * tg.nt);
-  const int X0 = I * W, Y0 = J * H, Z0 = K * D;
-  const bool full = (X0 - ns + 1 >= 0) && (Y0 - ns + 1 >= 0) && (Z0 - ns + 1 >= 0) && (X0 + W <= g.nx) &&
-                    (Y0 + H <= g.ny) && (Z0 + D <= g.nz);
-  const int64_t sx = g.sx, sy = g.sy;
-  const int64_t base = g.at(X0, Y0, Z0);
-  constexpr int NSITE = W * H * D;
-  for (int s = 0; s < ns; ++s) {
-    const int v = p * tg.nt + s;
-    const T* src = (v & 1) ? g_odd : g_even;
-    T* dst = (v & 1) ? g_even : g_odd;
-    const int64_t sb = base - (int64_t)s * (sy + sx + 1);
-#pragma unroll 2
-    for (int q = threadIdx.x; q < NSITE; q += TBJ_THREADS) {
-      const int ii = q % W, jj = (q / W) % H, kk = q / (W * H);
-      if (!full) {
-        const int x = X0 - s + ii, y = Y0 - s + jj, z = Z0 - s + kk;
-        if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz) continue;
-      }
-      const int64_t o = sb + (int64_t)kk * sy + (int64_t)jj * sx + ii;
-      T fv = T(0);
-      if (HAS_F) fv = f[o];
-      dst[o] = site_update<T, Ar, HAS_F, WEIGHTED>(src[o - 1], src[o + 1], src[o - sx], src[o + sx], src[o - sy],
-                                                   src[o + sy], fv, WEIGHTED ? src[o] : T(0), c);
-    }
-    __syncthreads();
-  }
+  jacobi_task_body<T, Ar, HAS_F, WEIGHTED, W, H, D>(g_even, g_odd, f, g, c, tg, I, J, K, p);
 }
 
 template <typename T, class Ar, bool HAS_F, bool WEIGHTED, int W, int H, int D>
@@ -108,6 +83,16 @@ int tb_jacobi_run(stencil_ctx* ctx, T* u, T* tmp, const T* f, const Geom& g, dou
   T* g_even = (nsweeps % 2) ? tmp : u;
   T* g_odd = (nsweeps % 2) ? u : tmp;
   int rc;
+  if (p->variant == 3) {
+    if (weighted) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "weighted Jacobi on the dataflow variant");
+    T* const a[1] = {g_even};
+    T* const b[1] = {g_odd};
+    const T* const fs[1] = {f};
+    const int ns[1] = {nsweeps};
+    const double hs[1] = {h};
+    return dataflow_run<T>(ctx, STENCIL_JACOBI, 1, a, b, fs, &g, ns, hs, tx, ty, tz, nt, ctx->df_timeout_ns,
+                           ctx->df_poison, st);
+  }
 #define TBJ_TILE(WW, HH, DD)                                                              \
   if (tx == WW && ty == HH && tz == DD) {                                                 \
     TileGeom tg = make_tile_geom(g, WW, HH, DD, nt, nsweeps);                             \

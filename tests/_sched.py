@@ -243,3 +243,90 @@ def jacobi_skewed_tiles(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int = 1,
             if k.size:
                 arr[(v + 1) % 2][k + 1, j + 1, i + 1] = _update(arr[v % 2], f, k, j, i, b, hh)
     return arr[nsweeps % 2]
+
+
+def dataflow_deps(I, J, K, p, nt, dims):
+    """Tasks a task waits for in the dataflow form of the skewed-tile schedule:
+    the three backward face neighbours of the same pass, and from the previous
+    pass the task itself and its forward face neighbours (nt = 1), or the eight
+    tiles (I+a, J+b, K+c), a, b, c in {0, 1} (nt > 1, whose shifted tiles end
+    inside this task's box).  dims = (NI, NJ, NK)."""
+    NI, NJ, NK = dims
+    out = []
+    for (a, b, c) in ((-1, 0, 0), (0, -1, 0), (0, 0, -1)):
+        if I + a >= 0 and J + b >= 0 and K + c >= 0:
+            out.append((I + a, J + b, K + c, p))
+    if p > 0:
+        if nt == 1:
+            prev = ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1))
+        else:
+            prev = [(a, b, c) for a in (0, 1) for b in (0, 1) for c in (0, 1)]
+        for (a, b, c) in prev:
+            if I + a < NI and J + b < NJ and K + c < NK:
+                out.append((I + a, J + b, K + c, p - 1))
+    return out
+
+
+def random_dataflow_order(nx, ny, nz, tile, nt, nsweeps, rng):
+    """A random linearisation of the dataflow dependency graph (Kahn's algorithm
+    choosing uniformly among ready tasks)."""
+    tasks, (NI, NJ, NK, npass) = skewed_tile_tasks(nx, ny, nz, tile, nt, nsweeps)
+    deps = {t: dataflow_deps(*t, nt, (NI, NJ, NK)) for t in tasks}
+    users = {t: [] for t in tasks}
+    for t, ds in deps.items():
+        for d in ds:
+            users[d].append(t)
+    missing = {t: len(ds) for t, ds in deps.items()}
+    ready = [t for t in tasks if missing[t] == 0]
+    order = []
+    while ready:
+        i = int(rng.integers(len(ready)))
+        t = ready[i]
+        ready[i] = ready[-1]
+        ready.pop()
+        order.append(t)
+        for w in users[t]:
+            missing[w] -= 1
+            if missing[w] == 0:
+                ready.append(w)
+    assert len(order) == len(tasks)
+    return order
+
+
+def run_task_order(kind, u, f, h, nsweeps, tile, nt, order):
+    """Run the tasks of the skewed-tile schedule in the given order (GS in place,
+    Jacobi with two parity arrays)."""
+    nz, ny, nx = (s - 2 for s in u.shape)
+    b, hh = _consts(u, h)
+    W, H, D = tile
+    if kind == "gs":
+        arr = [u.copy()]
+    else:
+        arr = [u.copy(), u.copy()]
+    jj_, ii_ = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    jj_, ii_ = jj_.ravel(), ii_.ravel()
+    kk3, jj3, ii3 = np.meshgrid(np.arange(D), np.arange(H), np.arange(W), indexing="ij")
+    kk3, jj3, ii3 = kk3.ravel(), jj3.ravel(), ii3.ravel()
+    for (I, J, K, p) in order:
+        ns = min(nt, nsweeps - p * nt)
+        X0, Y0, Z0 = I * W, J * H, K * D
+        if kind == "gs":
+            for lvl in range(-(ns - 1), W + H + D - 2):
+                ks, js, is_ = [], [], []
+                for s in range(ns):
+                    kk = lvl - ii_ - jj_ + s
+                    x, y, z = X0 - s + ii_, Y0 - s + jj_, Z0 - s + kk
+                    ok = (kk >= 0) & (kk < D) & (x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0) & (z < nz)
+                    ks.append(z[ok]); js.append(y[ok]); is_.append(x[ok])
+                k = np.concatenate(ks); j = np.concatenate(js); i = np.concatenate(is_)
+                if k.size:
+                    arr[0][k + 1, j + 1, i + 1] = _update(arr[0], f, k, j, i, b, hh)
+        else:
+            for s in range(ns):
+                v = p * nt + s
+                x, y, z = X0 - s + ii3, Y0 - s + jj3, Z0 - s + kk3
+                ok = (x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0) & (z < nz)
+                k, j, i = z[ok], y[ok], x[ok]
+                if k.size:
+                    arr[(v + 1) % 2][k + 1, j + 1, i + 1] = _update(arr[v % 2], f, k, j, i, b, hh)
+    return arr[0] if kind == "gs" else arr[nsweeps % 2]

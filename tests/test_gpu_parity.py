@@ -152,6 +152,70 @@ def test_gs_laplace_config1(ctx):
     _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, None, 1.0, 10), oracle.gs_lex(u0, None, 1.0, 10), "gs config1")
 
 
+# ------------------------------------------------- persistent dataflow kernel --
+@pytest.mark.parametrize("smoother", ["gs", "jacobi"])
+@pytest.mark.parametrize("nt", [1, 2, 4])
+@pytest.mark.parametrize("dims", [(45, 38, 29), (1, 1, 9), (64, 17, 5), (33, 9, 50)])
+def test_dataflow_single_grid(ctx, smoother, nt, dims):
+    """variant 3: one persistent launch over the dependency-ordered task queue."""
+    u0, f0 = W.random_grid(*dims, seed=nt + 40, with_f=True)
+    fn, ofn = (capi.stencil_gs_lex, oracle.gs_lex) if smoother == "gs" else (capi.stencil_jacobi, oracle.jacobi)
+    tile = (16, 16, 16) if smoother == "gs" else (32, 8, 8)
+    for ns in (1, 2 * nt + 1):
+        _assert_exact(_run(ctx, fn, u0, f0, 0.07, ns, nt=nt, tile=tile, variant=3), ofn(u0, f0, 0.07, ns),
+                      "dataflow %s nt=%d ns=%d %s" % (smoother, nt, ns, dims))
+
+
+def test_dataflow_f32_and_repeat(ctx):
+    u0, f0 = W.random_grid(70, 41, 33, seed=2, dtype=np.float32, with_f=True)
+    ref = oracle.gs_lex(u0, f0, 0.01, 9)
+    for _ in range(3):  # the cached plan and graph are replayed
+        _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.01, 9, nt=4, variant=3), ref, "f32 dataflow")
+
+
+@pytest.mark.parametrize("smoother", [capi.STENCIL_JACOBI, capi.STENCIL_GS])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("nt", [1, 2])
+def test_batched_uneven_grids(ctx, smoother, dtype, nt):
+    dims = [(32, 48, 16), (17, 5, 40), (64, 64, 32), (1, 1, 1), (48, 16, 80), (9, 33, 7)]
+    grids = [W.random_grid(*d, seed=i, dtype=dtype, with_f=(i % 2 == 0)) for i, d in enumerate(dims)]
+    hs = [W.grid_h(*d) for d in dims]
+    sweeps = [5, 4, 7, 3, 0, 6]
+    us = [_dev(u) for u, _ in grids]
+    fs = [_dev(f) for _, f in grids]
+    capi.stencil_batched(ctx, us, fs, hs, sweeps, smoother, nt=nt)
+    torch.cuda.synchronize()
+    ofn = oracle.jacobi if smoother == capi.STENCIL_JACOBI else oracle.gs_lex
+    for i, ((u0, f0), h, ns) in enumerate(zip(grids, hs, sweeps)):
+        _assert_exact(us[i].cpu().numpy(), ofn(u0, f0, h, ns), "batched grid %d" % i)
+
+
+def test_dataflow_wait_bound_reports_timeout():
+    """A task whose completion is never published: the bounded waits expire, the
+    call returns STENCIL_ERR_TIMEOUT, and the context keeps working."""
+    c = capi.Context(0)
+    u0, _ = W.random_grid(40, 40, 40, seed=1)
+    u = _dev(u0)
+    capi.stencil_set_wait_limit(c, 50_000_000, never_publish=3)
+    with pytest.raises(capi.StencilError) as e:
+        capi.stencil_gs_lex(c, u, None, 1.0, 4, variant=3)
+    assert e.value.code == capi.STENCIL_ERR_TIMEOUT
+    capi.stencil_set_wait_limit(c, 10_000_000_000, never_publish=-1)
+    _assert_exact(_run(c, capi.stencil_gs_lex, u0, None, 1.0, 4, variant=3), oracle.gs_lex(u0, None, 1.0, 4), "after")
+    c.close()
+
+
+@pytest.mark.parametrize("smoother", [capi.STENCIL_JACOBI, capi.STENCIL_GS])
+def test_autotune_picks_a_valid_config(ctx, smoother):
+    u0, f0 = W.random_grid(64, 48, 40, seed=3, with_f=True)
+    u = _dev(u0)
+    params, glups = capi.stencil_autotune(ctx, smoother, u, _dev(f0), 0.02, 8)
+    assert glups > 0
+    assert np.array_equal(u.cpu().numpy(), u0)  # the caller's grid is untouched
+    fn, ofn = (capi.stencil_gs_lex, oracle.gs_lex) if smoother == capi.STENCIL_GS else (capi.stencil_jacobi, oracle.jacobi)
+    _assert_exact(_run(ctx, fn, u0, f0, 0.02, 8, **params), ofn(u0, f0, 0.02, 8), "autotuned %s" % params)
+
+
 # ---------------------------------------------------------------- residual --
 @pytest.mark.parametrize("dims", [(37, 19, 23), (1, 1, 1), (64, 64, 64)])
 def test_residual_norm(ctx, dims):

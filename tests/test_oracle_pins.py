@@ -341,3 +341,42 @@ def test_skewed_tiles_depth_limit_is_sharp():
     ref_g, ref_j = oracle.gs_lex(u, f, 0.2, ns), oracle.jacobi(u, f, 0.2, ns)
     assert not np.array_equal(S.gs_skewed_tiles(u, f, 0.2, ns, (3, 3, 3), 4, True), ref_g)
     assert not np.array_equal(S.jacobi_skewed_tiles(u, f, 0.2, ns, (3, 3, 3), 4, True), ref_j)
+
+
+@pytest.mark.parametrize("tile,nt", [((4, 4, 4), 1), ((3, 2, 4), 1), ((4, 4, 4), 2), ((4, 3, 5), 3),
+                                     ((3, 3, 3), 3), ((2, 2, 2), 2)])
+def test_dataflow_orders_are_bit_exact(tile, nt):
+    """The persistent dataflow kernel runs a task once its dependencies
+    (tests/_sched.dataflow_deps) are done, in whatever order the hardware
+    picks: random linearisations of that dependency graph must all give the
+    serial result, for Gauss-Seidel in place and for Jacobi on two grids."""
+    rng = np.random.default_rng(0)
+    nx, ny, nz = 9, 7, 8
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    for ns in (1, 2 * nt + 1):
+        refs = {"gs": oracle.gs_lex(u, f, 0.2, ns), "jacobi": oracle.jacobi(u, f, 0.2, ns)}
+        for _ in range(4):
+            order = S.random_dataflow_order(nx, ny, nz, tile, nt, ns, rng)
+            for kind in ("gs", "jacobi"):
+                assert np.array_equal(S.run_task_order(kind, u, f, 0.2, ns, tile, nt, order), refs[kind])
+
+
+def test_dataflow_dependency_rule_is_sharp():
+    """With only face dependencies on the previous pass (too few for skewed
+    tiles), random orders break the result."""
+    rng = np.random.default_rng(1)
+    nx, ny, nz = 9, 7, 8
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    tile, nt, ns = (4, 4, 4), 2, 5
+    ref = oracle.gs_lex(u, f, 0.2, ns)
+    orig = S.dataflow_deps
+    try:
+        S.dataflow_deps = lambda I, J, K, p, nt_, dims: orig(I, J, K, p, 1, dims)
+        broken = sum(not np.array_equal(S.run_task_order("gs", u, f, 0.2, ns, tile, nt,
+                                                         S.random_dataflow_order(nx, ny, nz, tile, nt, ns, rng)), ref)
+                     for _ in range(4))
+    finally:
+        S.dataflow_deps = orig
+    assert broken > 0
