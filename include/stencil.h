@@ -184,6 +184,69 @@ int stencil_set_wait_limit(stencil_ctx* ctx, long long timeout_ns, long long nev
 int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, const void* f, const int64_t dims[3],
                      double h, int nsweeps, stencil_params* out, double* out_glups, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Continuous-batching server (not in the paper).
+ *
+ * A worker thread owns one GPU.  Each round it admits waiting requests in
+ * arrival order while their device memory fits hbm_budget_bytes (0 = no
+ * cap), copies their grids to the device where they stay until completion,
+ * runs up to sweeps_per_round sweeps (0 = 10) of every admitted request --
+ * all requests of one (smoother, dtype) class in ONE batched persistent
+ * launch -- tests solve requests' residuals, and copies finished grids back.
+ * Requests that arrive meanwhile join the next round.  A request's result is
+ * the same alone and in any mix.
+ * ------------------------------------------------------------------------- */
+#define STENCIL_PENDING 1 /* poll/wait: the request has not finished yet */
+
+#define STENCIL_REQ_JACOBI 0 /* nsweeps Jacobi sweeps */
+#define STENCIL_REQ_GS 1     /* nsweeps Gauss-Seidel sweeps */
+#define STENCIL_REQ_SOLVE 2  /* Gauss-Seidel sweeps until ||f-Au||/||f|| <= rtol, at most nsweeps (FP64 only) */
+
+typedef struct stencil_server stencil_server;
+
+typedef struct stencil_request {
+  int kind;          /* STENCIL_REQ_* */
+  int dtype;         /* STENCIL_F64 or STENCIL_F32 (solve: F64) */
+  int64_t dims[3];   /* interior extents, each >= 1 */
+  double h;          /* mesh width > 0 */
+  int nsweeps;       /* sweeps, or the sweep cap of a solve */
+  double rtol;       /* solve only */
+  const void* u_in;  /* HOST padded grid, read at admission; must stay valid until then */
+  const void* f_in;  /* HOST right-hand side or NULL (f = 0) */
+  void* u_out;       /* HOST buffer for the result or NULL; written before completion is reported */
+} stencil_request;
+
+typedef struct stencil_result {
+  int status;          /* STENCIL_OK, STENCIL_ERR_NOT_CONVERGED (solve capped), _CANCELLED, _OOM, ... */
+  int sweeps_done;
+  double rel_residual; /* solve: final relative residual; else -1 */
+  double queue_s;      /* submit -> admission */
+  double latency_s;    /* submit -> completion */
+} stencil_result;
+
+typedef struct stencil_server_stats {
+  uint64_t submitted, admitted, completed, cancelled, launches;
+  double p50_s, p99_s, mean_s; /* latency of completed requests */
+  double lup_total;            /* lattice-site updates performed */
+  double busy_s;               /* wall time of rounds */
+  double glups;                /* lup_total / busy_s / 1e9 */
+  size_t hbm_in_use, hbm_peak; /* request memory on the device */
+  int queue_depth, active;
+} stencil_server_stats;
+
+int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_bytes, int sweeps_per_round);
+/* Enqueue a request (copies the descriptor, not the grids); *ticket identifies it. */
+int stencil_server_submit(stencil_server* srv, const stencil_request* req, uint64_t* ticket);
+/* STENCIL_OK and *out filled if finished, STENCIL_PENDING if not. */
+int stencil_server_poll(stencil_server* srv, uint64_t ticket, stencil_result* out);
+/* Blocks up to timeout_s seconds; STENCIL_OK or STENCIL_PENDING. */
+int stencil_server_wait(stencil_server* srv, uint64_t ticket, double timeout_s, stencil_result* out);
+/* Cancels a request not yet admitted (its result: STENCIL_ERR_CANCELLED); STENCIL_ERR_ARG otherwise. */
+int stencil_server_cancel(stencil_server* srv, uint64_t ticket);
+int stencil_server_stats_get(stencil_server* srv, stencil_server_stats* out);
+/* Stops the worker after the current round and frees everything. */
+void stencil_server_destroy(stencil_server* srv);
+
 /* residual_norm without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc when they
  * need a residual (an application that owns all device memory through its

@@ -49,6 +49,30 @@ class stencil_params(ctypes.Structure):
                 ("a", ctypes.c_double), ("b", ctypes.c_double), ("variant", ctypes.c_int)]
 
 
+class stencil_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("h", ctypes.c_double),
+                ("nsweeps", ctypes.c_int), ("rtol", ctypes.c_double), ("u_in", ctypes.c_void_p),
+                ("f_in", ctypes.c_void_p), ("u_out", ctypes.c_void_p)]
+
+
+class stencil_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("sweeps_done", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("queue_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
+
+
+class stencil_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("launches", ctypes.c_uint64), ("p50_s", ctypes.c_double),
+                ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double), ("lup_total", ctypes.c_double),
+                ("busy_s", ctypes.c_double), ("glups", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t),
+                ("hbm_peak", ctypes.c_size_t), ("queue_depth", ctypes.c_int), ("active", ctypes.c_int)]
+
+
+STENCIL_PENDING = 1
+STENCIL_REQ_JACOBI = 0
+STENCIL_REQ_GS = 1
+STENCIL_REQ_SOLVE = 2
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -72,6 +96,13 @@ _SIGS = {
                              ctypes.POINTER(_I), _I, _I, _PP, _P]),
     "stencil_set_wait_limit": (_I, [_P, ctypes.c_longlong, ctypes.c_longlong]),
     "stencil_autotune": (_I, [_P, _I, _I, _P, _P, _I64P, _D, _I, _PP, ctypes.POINTER(_D), _P]),
+    "stencil_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I]),
+    "stencil_server_submit": (_I, [_P, ctypes.POINTER(stencil_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "stencil_server_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(stencil_result)]),
+    "stencil_server_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(stencil_result)]),
+    "stencil_server_cancel": (_I, [_P, ctypes.c_uint64]),
+    "stencil_server_stats_get": (_I, [_P, ctypes.POINTER(stencil_server_stats)]),
+    "stencil_server_destroy": (None, [_P]),
     "residual_norm_noalloc": (_I, [_P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stencil_solve_mixed": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
     "stencil_solve_f64": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, _PP, ctypes.POINTER(_D), ctypes.POINTER(_I),
@@ -310,3 +341,92 @@ def stencil_solve_f64(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: 
                                ctypes.byref(p), ctypes.byref(rel), ctypes.byref(sw), _stream(stream))
     _check(ctx, rc, allow=(STENCIL_ERR_NOT_CONVERGED,))
     return rel.value, sw.value, rc == STENCIL_OK
+
+
+# ------------------------------------------------------------------ server --
+def _result_dict(r: stencil_result) -> dict:
+    return {"status": r.status, "sweeps_done": r.sweeps_done, "rel_residual": r.rel_residual, "queue_s": r.queue_s,
+            "latency_s": r.latency_s}
+
+
+class Server:
+    """Continuous-batching server (stencil_server_*).  Grids are host numpy
+    arrays of shape (nz+2, ny+2, nx+2), float64 or float32; they are referenced
+    (not copied) until the request completes."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, sweeps_per_round: int = 10):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        rc = lib.stencil_server_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), int(sweeps_per_round))
+        if rc != STENCIL_OK:
+            raise StencilError(rc, (lib.stencil_last_error(None) or b"").decode())
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, kind: int, u_in, f_in=None, h: float = 1.0, nsweeps: int = 1, rtol: float = 0.0,
+               u_out=None) -> int:
+        import numpy as np
+
+        for a in (u_in, f_in, u_out):
+            if a is not None and (not isinstance(a, np.ndarray) or not a.flags.c_contiguous):
+                raise ValueError("grids must be C-contiguous numpy arrays")
+        r = stencil_request()
+        r.kind = int(kind)
+        r.dtype = STENCIL_F64 if u_in.dtype == np.float64 else STENCIL_F32
+        nz, ny, nx = (int(x) - 2 for x in u_in.shape)
+        r.dims[0], r.dims[1], r.dims[2] = nx, ny, nz
+        r.h, r.nsweeps, r.rtol = float(h), int(nsweeps), float(rtol)
+        r.u_in = u_in.ctypes.data
+        r.f_in = None if f_in is None else f_in.ctypes.data
+        r.u_out = None if u_out is None else u_out.ctypes.data
+        t = ctypes.c_uint64(0)
+        rc = load_library().stencil_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t))
+        if rc != STENCIL_OK:
+            raise StencilError(rc, "submit rejected")
+        self._keep[t.value] = (u_in, f_in, u_out)
+        return t.value
+
+    def poll(self, ticket: int):
+        res = stencil_result()
+        rc = load_library().stencil_server_poll(self.handle, ticket, ctypes.byref(res))
+        if rc == STENCIL_PENDING:
+            return None
+        if rc != STENCIL_OK:
+            raise StencilError(rc, "poll")
+        self._keep.pop(ticket, None)
+        return _result_dict(res)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        res = stencil_result()
+        rc = load_library().stencil_server_wait(self.handle, ticket, float(timeout_s), ctypes.byref(res))
+        if rc == STENCIL_PENDING:
+            return None
+        if rc != STENCIL_OK:
+            raise StencilError(rc, "wait")
+        self._keep.pop(ticket, None)
+        return _result_dict(res)
+
+    def cancel(self, ticket: int) -> bool:
+        return load_library().stencil_server_cancel(self.handle, ticket) == STENCIL_OK
+
+    def stats(self) -> dict:
+        st = stencil_server_stats()
+        _check(None, load_library().stencil_server_stats_get(self.handle, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in stencil_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().stencil_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,381 @@
+// Continuous-batching server for smoothing and solve requests (not in the
+// paper; it serves the smoothers to many concurrent users of one GPU).
+//
+// A worker thread owns the GPU work.  Each round it (1) admits waiting
+// requests in arrival order while their device memory fits the HBM budget,
+// copying their grids to the device, where they stay until the request
+// completes; (2) runs up to `sweeps_per_round` sweeps of every admitted
+// request, all requests of one (smoother, dtype) class in ONE persistent
+// batched launch (stencil_batched); (3) checks solve requests' residuals;
+// (4) copies finished grids back and frees their memory.  Requests that
+// arrive while a round runs join the next round, as slots and memory free up.
+// A request's result does not depend on the other requests in the mix: the
+// batched kernel is exact per grid, sweeps split into rounds compose exactly,
+// and solve requests test their residual after every `sweeps_per_round`
+// sweeps whatever else is running.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+struct stencil_server;
+
+namespace stn {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t ticket;
+  stencil_request r;
+  Clock::time_point t_submit, t_admit, t_done;
+  size_t bytes = 0;
+  void* du = nullptr;
+  void* df = nullptr;
+  int done_sweeps = 0;
+  int state = 0;  // 0 waiting, 1 active, 2 finished
+  stencil_result res{};
+};
+
+}  // namespace stn
+
+using namespace stn;
+
+struct stencil_server {
+  stencil_ctx* ctx = nullptr;
+  size_t budget = 0;
+  int quantum = 10;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> waiting;
+  std::map<uint64_t, Req*> reqs;
+  std::vector<uint64_t> active;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  size_t in_use = 0, peak = 0;
+  stencil_server_stats st{};
+  std::vector<double> lat;
+  double busy_s = 0.0, lup = 0.0;
+  std::string err;
+};
+
+namespace stn {
+
+static size_t req_bytes(const stencil_request& r) {
+  const size_t n = (size_t)(r.dims[0] + 2) * (size_t)(r.dims[1] + 2) * (size_t)(r.dims[2] + 2);
+  const size_t esz = r.dtype == STENCIL_F64 ? 8 : 4;
+  size_t b = n * esz;                      // u
+  if (r.f_in) b += n * esz;                // f
+  if (r.kind == STENCIL_REQ_JACOBI) b += n * esz;  // second Jacobi grid (batch workspace)
+  return b;
+}
+
+static void finish(stencil_server* s, Req* q, int status, double rel) {
+  q->t_done = Clock::now();
+  q->res.status = status;
+  q->res.sweeps_done = q->done_sweeps;
+  q->res.rel_residual = rel;
+  q->res.queue_s = std::chrono::duration<double>(q->t_admit - q->t_submit).count();
+  q->res.latency_s = std::chrono::duration<double>(q->t_done - q->t_submit).count();
+  q->state = 2;
+}
+
+// One round of the worker; returns false when there is nothing to do.
+static bool server_round(stencil_server* s) {
+  std::vector<Req*> admit;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->waiting.empty()) {
+      Req* q = s->reqs[s->waiting.front()];
+      if (s->budget && q->bytes > s->budget) {  // can never fit
+        s->waiting.pop_front();
+        q->t_admit = Clock::now();
+        finish(s, q, STENCIL_ERR_OOM, -1.0);
+        s->cv_done.notify_all();
+        continue;
+      }
+      if (s->budget && s->in_use + q->bytes > s->budget) break;  // wait, in arrival order, for memory
+      s->waiting.pop_front();
+      s->in_use += q->bytes;
+      s->peak = std::max(s->peak, s->in_use);
+      q->t_admit = Clock::now();
+      q->state = 1;
+      admit.push_back(q);
+      s->active.push_back(q->ticket);
+      s->st.admitted++;
+    }
+  }
+  stencil_ctx* ctx = s->ctx;
+  cudaStream_t st = ctx->gstream;
+  // upload admitted grids
+  for (Req* q : admit) {
+    const size_t n = (size_t)(q->r.dims[0] + 2) * (size_t)(q->r.dims[1] + 2) * (size_t)(q->r.dims[2] + 2);
+    const size_t esz = q->r.dtype == STENCIL_F64 ? 8 : 4;
+    cudaError_t e = cudaMalloc(&q->du, n * esz);
+    if (e == cudaSuccess && q->r.f_in) e = cudaMalloc(&q->df, n * esz);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q->du, q->r.u_in, n * esz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && q->df) e = cudaMemcpyAsync(q->df, q->r.f_in, n * esz, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      std::lock_guard<std::mutex> lk(s->mu);
+      finish(s, q, STENCIL_ERR_OOM, -1.0);
+    }
+  }
+  std::vector<Req*> act;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (uint64_t t : s->active) {
+      Req* q = s->reqs[t];
+      if (q->state == 1) act.push_back(q);
+    }
+  }
+  if (act.empty()) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->active.clear();
+    return !admit.empty();
+  }
+  const auto t0 = Clock::now();
+  // one batched launch per (smoother, dtype) class
+  for (int cls = 0; cls < 4; ++cls) {
+    const int smoother = cls / 2 == 0 ? STENCIL_JACOBI : STENCIL_GS;
+    const int dtype = cls % 2 == 0 ? STENCIL_F64 : STENCIL_F32;
+    std::vector<Req*> grp;
+    for (Req* q : act) {
+      const int sm = q->r.kind == STENCIL_REQ_JACOBI ? STENCIL_JACOBI : STENCIL_GS;
+      if (sm == smoother && q->r.dtype == dtype && q->state == 1) grp.push_back(q);
+    }
+    if (grp.empty()) continue;
+    std::vector<void*> u;
+    std::vector<const void*> f;
+    std::vector<int64_t> dims;
+    std::vector<double> h;
+    std::vector<int> ns;
+    for (Req* q : grp) {
+      u.push_back(q->du);
+      f.push_back(q->df);
+      dims.insert(dims.end(), q->r.dims, q->r.dims + 3);
+      h.push_back(q->r.h);
+      ns.push_back(std::min(s->quantum, q->r.nsweeps - q->done_sweeps));
+    }
+    int rc = stencil_batched(ctx, (int)grp.size(), u.data(), f.data(), dims.data(), h.data(), ns.data(), smoother,
+                             dtype, nullptr, st);
+    s->st.launches++;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (size_t i = 0; i < grp.size(); ++i) {
+      Req* q = grp[i];
+      if (rc != STENCIL_OK) {
+        finish(s, q, rc, -1.0);
+        continue;
+      }
+      q->done_sweeps += ns[i];
+      s->lup += (double)q->r.dims[0] * q->r.dims[1] * q->r.dims[2] * ns[i];
+    }
+  }
+  // solve requests: residual after every round
+  for (Req* q : act) {
+    if (q->state != 1) continue;
+    Geom g = make_geom((int)q->r.dims[0], (int)q->r.dims[1], (int)q->r.dims[2]);
+    if (q->r.kind == STENCIL_REQ_SOLVE) {
+      double ab = 0.0, rel = 0.0;
+      int rc = residual_norm(ctx, (const double*)q->du, (const double*)q->df, q->r.dims, q->r.h, nullptr, &ab, &rel,
+                             st);
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (rc != STENCIL_OK)
+        finish(s, q, rc, -1.0);
+      else if (rel <= q->r.rtol)
+        finish(s, q, STENCIL_OK, rel);
+      else if (q->done_sweeps >= q->r.nsweeps)
+        finish(s, q, STENCIL_ERR_NOT_CONVERGED, rel);
+    } else if (q->done_sweeps >= q->r.nsweeps) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      finish(s, q, STENCIL_OK, -1.0);
+    }
+    (void)g;
+  }
+  cudaStreamSynchronize(st);
+  s->busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
+  // retire finished requests
+  std::vector<Req*> fin;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::vector<uint64_t> keep;
+    for (uint64_t t : s->active) {
+      Req* q = s->reqs[t];
+      if (q->state == 2)
+        fin.push_back(q);
+      else
+        keep.push_back(t);
+    }
+    s->active.swap(keep);
+  }
+  for (Req* q : fin) {
+    const size_t n = (size_t)(q->r.dims[0] + 2) * (size_t)(q->r.dims[1] + 2) * (size_t)(q->r.dims[2] + 2);
+    const size_t esz = q->r.dtype == STENCIL_F64 ? 8 : 4;
+    if (q->r.u_out && q->du && (q->res.status == STENCIL_OK || q->res.status == STENCIL_ERR_NOT_CONVERGED))
+      cudaMemcpy(q->r.u_out, q->du, n * esz, cudaMemcpyDeviceToHost);
+    if (q->du) cudaFree(q->du);
+    if (q->df) cudaFree(q->df);
+    q->du = q->df = nullptr;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->in_use -= q->bytes;
+    q->t_done = Clock::now();
+    q->res.latency_s = std::chrono::duration<double>(q->t_done - q->t_submit).count();
+    s->lat.push_back(q->res.latency_s);
+    s->st.completed++;
+  }
+  if (!fin.empty()) s->cv_done.notify_all();
+  return true;
+}
+
+static void server_main(stencil_server* s) {
+  cudaSetDevice(s->ctx->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_work.wait_for(lk, std::chrono::milliseconds(50),
+                          [&] { return s->stop || !s->waiting.empty() || !s->active.empty(); });
+      if (s->stop) break;
+      if (s->waiting.empty() && s->active.empty()) continue;
+    }
+    server_round(s);
+  }
+}
+
+}  // namespace stn
+
+extern "C" {
+
+int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_bytes, int sweeps_per_round) {
+  if (!out || sweeps_per_round < 0) return STENCIL_ERR_ARG;
+  *out = nullptr;
+  stencil_ctx* ctx = nullptr;
+  int rc = stencil_create(&ctx, device, 0);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    stencil_destroy(ctx);
+    return set_err(nullptr, STENCIL_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+  }
+  stencil_server* s = new stencil_server();
+  s->ctx = ctx;
+  s->budget = hbm_budget_bytes;
+  s->quantum = sweeps_per_round > 0 ? sweeps_per_round : 10;
+  s->worker = std::thread(server_main, s);
+  *out = s;
+  return STENCIL_OK;
+}
+
+int stencil_server_submit(stencil_server* s, const stencil_request* r, uint64_t* ticket) {
+  if (!s || !r || !ticket) return STENCIL_ERR_ARG;
+  if (r->kind < STENCIL_REQ_JACOBI || r->kind > STENCIL_REQ_SOLVE) return STENCIL_ERR_ARG;
+  if (r->dtype != STENCIL_F64 && r->dtype != STENCIL_F32) return STENCIL_ERR_ARG;
+  if (r->kind == STENCIL_REQ_SOLVE && (r->dtype != STENCIL_F64 || !(r->rtol > 0.0))) return STENCIL_ERR_ARG;
+  if (!r->u_in || r->nsweeps < 0 || !(r->h > 0.0)) return STENCIL_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (r->dims[d] < 1 || r->dims[d] > (1 << 20)) return STENCIL_ERR_ARG;
+  Req* q = new Req();
+  q->r = *r;
+  q->t_submit = Clock::now();
+  q->bytes = req_bytes(*r);
+  q->res.rel_residual = -1.0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    q->ticket = s->next_ticket++;
+    s->reqs[q->ticket] = q;
+    s->waiting.push_back(q->ticket);
+    s->st.submitted++;
+    *ticket = q->ticket;
+  }
+  s->cv_work.notify_one();
+  return STENCIL_OK;
+}
+
+int stencil_server_poll(stencil_server* s, uint64_t ticket, stencil_result* out) {
+  if (!s || !out) return STENCIL_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return STENCIL_ERR_ARG;
+  Req* q = it->second;
+  if (q->state != 2 || q->du) return STENCIL_PENDING;
+  *out = q->res;
+  return STENCIL_OK;
+}
+
+int stencil_server_wait(stencil_server* s, uint64_t ticket, double timeout_s, stencil_result* out) {
+  if (!s || !out) return STENCIL_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return STENCIL_ERR_ARG;
+  Req* q = it->second;
+  const auto until = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+  while (q->state != 2 || q->du) {
+    if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout && (q->state != 2 || q->du)) return STENCIL_PENDING;
+  }
+  *out = q->res;
+  return STENCIL_OK;
+}
+
+int stencil_server_cancel(stencil_server* s, uint64_t ticket) {
+  if (!s) return STENCIL_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return STENCIL_ERR_ARG;
+  Req* q = it->second;
+  if (q->state != 0) return STENCIL_ERR_ARG;  // already admitted
+  s->waiting.erase(std::remove(s->waiting.begin(), s->waiting.end(), ticket), s->waiting.end());
+  q->t_admit = Clock::now();
+  finish(s, q, STENCIL_ERR_CANCELLED, -1.0);
+  s->st.cancelled++;
+  s->cv_done.notify_all();
+  return STENCIL_OK;
+}
+
+int stencil_server_stats_get(stencil_server* s, stencil_server_stats* out) {
+  if (!s || !out) return STENCIL_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->st;
+  std::vector<double> l = s->lat;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double p) { return l.empty() ? 0.0 : l[std::min(l.size() - 1, (size_t)(p * (l.size() - 1) + 0.5))]; };
+  out->p50_s = pct(0.50);
+  out->p99_s = pct(0.99);
+  double sum = 0.0;
+  for (double x : l) sum += x;
+  out->mean_s = l.empty() ? 0.0 : sum / l.size();
+  out->lup_total = s->lup;
+  out->busy_s = s->busy_s;
+  out->glups = s->busy_s > 0 ? s->lup / s->busy_s / 1e9 : 0.0;
+  out->hbm_in_use = s->in_use;
+  out->hbm_peak = s->peak;
+  out->queue_depth = (int)s->waiting.size();
+  out->active = (int)s->active.size();
+  return STENCIL_OK;
+}
+
+void stencil_server_destroy(stencil_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  cudaSetDevice(s->ctx->device);
+  for (auto& kv : s->reqs) {
+    Req* q = kv.second;
+    if (q->du) cudaFree(q->du);
+    if (q->df) cudaFree(q->df);
+    delete q;
+  }
+  stencil_destroy(s->ctx);
+  delete s;
+}
+
+}  // extern "C"
