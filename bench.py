@@ -30,8 +30,8 @@ N = 400
 SWEEPS = 100
 # the launch configuration timed for the headline (tests/test_gpu_parity.py checks it at full size)
 HEADLINE = {
-    "jacobi": {"nt": 1, "tile": (32, 8, 0)},
-    "gs": {"nt": 1, "tile": (16, 16, 16)},
+    "jacobi": {"nt": 1, "tile": (32, 4, 0)},
+    "gs": {"nt": 4, "tile": (32, 8, 8)},
 }
 NT_SWEEP = [1, 2, 4, 8, 16]
 METRIC = "GLUP/s at 400^3 FP64 (Jacobi, GS) vs HBM roofline; batched/served vs plain, p99"
@@ -283,6 +283,9 @@ def run_gpu(args):
     if not args.skip_nt_sweep:
         details["nt_sweep"] = nt_sweep(ctx, capi, torch, uj, ug, stream)
 
+    if not args.skip_batched:
+        details["batched_256"] = batched_compare(ctx, capi, torch, dev, stream)
+
     # end to end through the public API: pinned host -> device, run, device -> host
     e2e = None
     if not args.skip_e2e:
@@ -333,11 +336,13 @@ def launch_counts(ctx, smoother, cfg):
 def nt_sweep(ctx, capi, torch, uj, ug, stream):
     out = {}
     for name, fn, u, cfg in (("jacobi", capi.stencil_jacobi, uj, HEADLINE["jacobi"]),
-                             ("gs", capi.stencil_gs_lex, ug, HEADLINE["gs"])):
+                             ("gs", capi.stencil_gs_lex, ug, HEADLINE["gs"]),
+                             ("jacobi_f32", capi.stencil_jacobi, uj.float(), HEADLINE["jacobi"]),
+                             ("gs_f32", capi.stencil_gs_lex, ug.float(), HEADLINE["gs"])):
         res = {}
         for nt in NT_SWEEP:
             try:
-                tile = cfg["tile"] if nt == 1 else (0, 0, 0)
+                tile = cfg["tile"] if nt == cfg["nt"] else (0, 0, 0)
                 fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, stream=stream)  # warm
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
@@ -346,10 +351,50 @@ def nt_sweep(ctx, capi, torch, uj, ug, stream):
                 torch.cuda.synchronize()
                 t = a.elapsed_time(b) / 1e3
                 res[str(nt)] = {"glups": SWEEPS * N ** 3 / t / 1e9, "ms": t * 1e3,
-                                "alg_bytes_per_lup": 16.0 / nt}
+                                "alg_bytes_per_lup": (8.0 if u.dtype == torch.float32 else 16.0) / nt}
             except capi.StencilError as e:
                 res[str(nt)] = {"unsupported": str(e)}
         out[name] = res
+    return out
+
+
+def batched_compare(ctx, capi, torch, dev, stream, count=256):
+    """256 uneven Poisson grids (extents multiples of 16 in [32,192], seed 3): the
+    plain per-grid loop of single-grid calls vs one batched persistent launch,
+    50 Jacobi and 20 Gauss-Seidel sweeps, FP64."""
+    from paper_1004_1741_gb300 import workloads
+
+    cases = workloads.batched_poisson(count)
+    us = [torch.from_numpy(c.u).to(dev) for c in cases]
+    fs = [torch.from_numpy(c.f).to(dev) for c in cases]
+    hs = [c.h for c in cases]
+    saved = [u.clone() for u in us]
+    sites = float(sum(c.nx * c.ny * c.nz for c in cases))
+    out = {"grids": count, "sites": sites}
+
+    def timed(fn):
+        for u, s0 in zip(us, saved):
+            u.copy_(s0)
+        fn()  # warm (tables, plans, graphs)
+        for u, s0 in zip(us, saved):
+            u.copy_(s0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    for name, sm, sweeps, single in (("jacobi", capi.STENCIL_JACOBI, 50, capi.stencil_jacobi),
+                                     ("gs", capi.STENCIL_GS, 20, capi.stencil_gs_lex)):
+        t_plain = timed(lambda: [single(ctx, u, f, h, sweeps, stream=stream) for u, f, h in zip(us, fs, hs)])
+        t_batch = timed(lambda: capi.stencil_batched(ctx, us, fs, hs, [sweeps] * count, sm, stream=stream))
+        lup = sites * sweeps
+        out[name] = {"sweeps": sweeps, "plain_glups": lup / t_plain / 1e9, "batched_glups": lup / t_batch / 1e9,
+                     "speedup": t_plain / t_batch}
+    del us, fs, saved
+    torch.cuda.empty_cache()
     return out
 
 
@@ -409,6 +454,118 @@ def run_case(args):
     return 0
 
 
+def run_suite_mixed(args):
+    """Mixed-precision defect correction vs FP64-only sweeps on the 512^3 sine-mode
+    Poisson problem (8 modes + N(0,1e-3) noise, seed 4), compared at equal final
+    residual: the FP64 solve runs a fixed sweep budget, the mixed solve runs until it
+    reaches the same relative residual."""
+    import torch
+
+    from paper_1004_1741_gb300 import capi, workloads
+
+    n = args.n if args.n != 320 else 512
+    prob = workloads.sine_modes_problem(n, seed=4)
+    dev = torch.device("cuda", 0)
+    ctx = capi.Context(0)
+    f = torch.from_numpy(prob.f).to(dev)
+    res = {}
+    for name, sm in (("jacobi", capi.STENCIL_JACOBI), ("gs", capi.STENCIL_GS)):
+        budget, check = args.sweeps if args.sweeps != 8 else 200, 20
+        u = torch.zeros_like(f)
+        capi.stencil_solve_f64(ctx, u, f, prob.h, sm, 0.0, check, check)  # warm
+        u.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rel64, sw, _ = capi.stencil_solve_f64(ctx, u, f, prob.h, sm, 0.0, budget, check)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        u2 = torch.zeros_like(f)
+        capi.stencil_solve_mixed(ctx, u2, f, prob.h, sm, 0.5, 1, check)  # warm
+        u2.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        relm, outer, ok = capi.stencil_solve_mixed(ctx, u2, f, prob.h, sm, rel64, 10 * budget // check, check)
+        torch.cuda.synchronize()
+        tm = time.perf_counter() - t0
+        diff = float((u2 - u).abs().max().item())
+        res[name] = {"fp64": {"sweeps": sw, "rel": rel64, "s": t64, "glups": n ** 3 * sw / t64 / 1e9},
+                     "mixed": {"outer": outer, "inner_sweeps": check, "rel": relm, "reached": ok, "s": tm,
+                               "sweep_glups": n ** 3 * outer * check / tm / 1e9},
+                     "speedup_at_equal_residual": t64 / tm, "max_abs_diff_u": diff,
+                     "max_abs_u": float(u.abs().max().item())}
+    line = {"suite": "mixed", "metric": "time to equal relative residual, 512^3 Poisson (FP32 inner sweeps + FP64 "
+                                         "defect correction vs FP64 sweeps)", "n": n, "unit": "s",
+            "data": "synthetic", "results": res}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_suite_served(args):
+    """Served stream: Poisson arrivals of smoothing and solve requests (sides
+    log-uniform in [32, 384], rounded to multiples of 16; 10-200 sweeps or a solve
+    to 1e-8 capped at 2000 sweeps; FP64/FP32), 150 GB HBM budget, for a range of
+    arrival rates; p50/p99 latency, GLUP/s, admitted/cancelled per rate.  At most
+    --slots requests are admitted at once; at the end of the arrival window the
+    requests never admitted are cancelled (counted) and the admitted ones drain."""
+    import numpy as np
+
+    from paper_1004_1741_gb300 import capi, workloads
+
+    rates = [float(x) for x in args.rates.split(",")]
+    window = args.window
+    pool = {}
+
+    def inputs(nn, dt):
+        key = (nn, dt)
+        if key not in pool:
+            rng = np.random.default_rng(nn)
+            u = rng.random((nn + 2,) * 3)
+            u[1:-1, 1:-1, 1:-1] = 0.0
+            fz = np.zeros_like(u)
+            fz[1:-1, 1:-1, 1:-1] = rng.standard_normal((nn,) * 3)
+            pool[key] = (np.ascontiguousarray(u.astype(dt)), np.ascontiguousarray(fz.astype(dt)))
+        return pool[key]
+
+    out = []
+    for rate in rates:
+        reqs = workloads.served_stream(rate, max(1, int(rate * window * 1.2)), seed=5)
+        with capi.Server(0, hbm_budget_bytes=150 * 10 ** 9, sweeps_per_round=10, max_active=args.slots) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for r in reqs:
+                if r.arrival_s > window:
+                    break
+                now = time.perf_counter() - t0
+                if r.arrival_s > now:
+                    time.sleep(r.arrival_s - now)
+                nn = max(32, min(384, 16 * round(r.n / 16)))
+                dt = np.float64 if (r.dtype == "f64" or r.kind == "solve") else np.float32
+                u, fz = inputs(nn, dt)
+                kind = {"jacobi": capi.STENCIL_REQ_JACOBI, "gs": capi.STENCIL_REQ_GS, "solve": capi.STENCIL_REQ_SOLVE}[r.kind]
+                tickets.append(srv.submit(kind, u, fz, 1.0 / (nn + 1), r.sweeps, rtol=r.rtol))
+            t_arr = time.perf_counter() - t0
+            # end of the window: what was never admitted is cancelled, admitted work drains
+            for t in tickets:
+                srv.cancel(t)
+            results = [srv.wait(t, args.drain) for t in tickets]
+            st = srv.stats()
+        done = [r for r in results if r and r["status"] in (capi.STENCIL_OK, capi.STENCIL_ERR_NOT_CONVERGED)]
+        if any(r is None for r in results):
+            raise RuntimeError("served requests did not drain within %.0f s" % args.drain)
+        lat = sorted(r["latency_s"] for r in done)
+        pct = (lambda q: lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None)
+        out.append({"rate_hz": rate, "submitted": len(tickets), "completed": len(done),
+                    "cancelled": sum(1 for r in results if r and r["status"] == capi.STENCIL_ERR_CANCELLED),
+                    "p50_s": pct(0.5), "p99_s": pct(0.99), "glups": st["glups"], "lup": st["lup_total"],
+                    "busy_s": st["busy_s"], "arrival_window_s": t_arr, "hbm_peak_gb": st["hbm_peak"] / 1e9,
+                    "launches": st["launches"]})
+    line = {"suite": "served", "metric": "p50/p99 latency and GLUP/s vs arrival rate (continuous batching)",
+            "unit": "s", "data": "synthetic", "window_s": window, "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,6 +575,7 @@ def main():
     ap.add_argument("--skip-nt-sweep", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--case", choices=["jacobi", "gs"], help="run one smoother only (profiling case)")
     ap.add_argument("--n", type=int, default=320)
     ap.add_argument("--sweeps", type=int, default=8)
@@ -425,9 +583,18 @@ def main():
     ap.add_argument("--tile", default="")
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--suite", choices=["mixed", "served"], help="a secondary workload instead of the headline")
+    ap.add_argument("--rates", default="50,100,200,500,1000,2000")
+    ap.add_argument("--window", type=float, default=3.0)
+    ap.add_argument("--drain", type=float, default=60.0)
+    ap.add_argument("--slots", type=int, default=32)
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.suite == "mixed":
+        return run_suite_mixed(args)
+    if args.suite == "served":
+        return run_suite_served(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -189,7 +189,7 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
  *
  * A worker thread owns one GPU.  Each round it admits waiting requests in
  * arrival order while their device memory fits hbm_budget_bytes (0 = no
- * cap), copies their grids to the device where they stay until completion,
+ * cap) and fewer than max_active requests are admitted (0 = no slot limit), copies their grids to the device where they stay until completion,
  * runs up to sweeps_per_round sweeps (0 = 10) of every admitted request --
  * all requests of one (smoother, dtype) class in ONE batched persistent
  * launch -- tests solve requests' residuals, and copies finished grids back.
@@ -234,7 +234,8 @@ typedef struct stencil_server_stats {
   int queue_depth, active;
 } stencil_server_stats;
 
-int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_bytes, int sweeps_per_round);
+int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_bytes, int sweeps_per_round,
+                          int max_active);
 /* Enqueue a request (copies the descriptor, not the grids); *ticket identifies it. */
 int stencil_server_submit(stencil_server* srv, const stencil_request* req, uint64_t* ticket);
 /* STENCIL_OK and *out filled if finished, STENCIL_PENDING if not. */

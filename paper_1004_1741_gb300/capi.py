@@ -96,7 +96,7 @@ _SIGS = {
                              ctypes.POINTER(_I), _I, _I, _PP, _P]),
     "stencil_set_wait_limit": (_I, [_P, ctypes.c_longlong, ctypes.c_longlong]),
     "stencil_autotune": (_I, [_P, _I, _I, _P, _P, _I64P, _D, _I, _PP, ctypes.POINTER(_D), _P]),
-    "stencil_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I]),
+    "stencil_server_create": (_I, [ctypes.POINTER(_P), _I, ctypes.c_size_t, _I, _I]),
     "stencil_server_submit": (_I, [_P, ctypes.POINTER(stencil_request), ctypes.POINTER(ctypes.c_uint64)]),
     "stencil_server_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(stencil_result)]),
     "stencil_server_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(stencil_result)]),
@@ -354,10 +354,11 @@ class Server:
     arrays of shape (nz+2, ny+2, nx+2), float64 or float32; they are referenced
     (not copied) until the request completes."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, sweeps_per_round: int = 10):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, sweeps_per_round: int = 10, max_active: int = 0):
         lib = load_library()
         h = ctypes.c_void_p()
-        rc = lib.stencil_server_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), int(sweeps_per_round))
+        rc = lib.stencil_server_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), int(sweeps_per_round),
+                                       int(max_active))
         if rc != STENCIL_OK:
             raise StencilError(rc, (lib.stencil_last_error(None) or b"").decode())
         self.handle = h

@@ -70,42 +70,159 @@ __global__ void __launch_bounds__(32 * BY) jacobi_zmarch_kernel(const T* __restr
   }
 }
 
+// Pipelined variant: the same 2.5D z-march, but planes arrive in shared
+// memory through asynchronous copies (cp.async) issued PF = S-4 planes ahead
+// into a ring of S plane buffers, so each CTA keeps several planes of loads
+// in flight.  Bandwidth-bound FP32 sweeps need that memory-level parallelism;
+// the FP64 sweep is FP64-pipe-bound either way.  One barrier per plane: the
+// buffer a new copy fills was last read two iterations earlier.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename T, class Ar, bool HAS_F, bool WEIGHTED, int BY, int S>
+__global__ void __launch_bounds__(32 * BY) jacobi_pipe_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                                              const T* __restrict__ f, Geom g, int zchunk, Coef<T> c) {
+  constexpr int PF = S - 4;
+  static_assert(PF >= 1, "ring too small");
+  __shared__ T ring[S][BY + 2][32 + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x = blockIdx.x * 32 + tx;
+  const int y = blockIdx.y * BY + ty;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(g.nz, z0 + zchunk);
+  if (z0 >= z1) return;
+  const bool inside = (x <= g.nx) && (y <= g.ny);
+  const bool active = (x < g.nx) && (y < g.ny);
+  const bool hw = (tx == 0) && (y <= g.ny);
+  const bool he = (tx == 31) && (x + 1 <= g.nx) && (y <= g.ny);
+  const bool hs = (ty == 0) && (x <= g.nx);
+  const bool hn = (ty == BY - 1) && (y + 1 <= g.ny) && (x <= g.nx);
+  const int64_t sy = g.sy;
+  const int64_t col = inside ? g.at(x, y, -1) : 0;
+  const int64_t colw = hw ? g.at(x - 1, y, -1) : 0;
+  const int64_t cole = he ? g.at(x + 1, y, -1) : 0;
+  const int64_t cols = hs ? g.at(x, y - 1, -1) : 0;
+  const int64_t coln = hn ? g.at(x, y + 1, -1) : 0;
+  // plane q (interior index, -1..nz) lives in ring[(q - z0 + 1) % S]
+  auto issue = [&](int q) {
+    if (q <= z1) {
+      const int sl = (q - z0 + 1) % S;
+      const int64_t pz = (int64_t)(q + 1) * sy;
+      if (inside) cp_async_elem(&ring[sl][ty + 1][tx + 1], src + col + pz);
+      if (hw) cp_async_elem(&ring[sl][ty + 1][0], src + colw + pz);
+      if (he) cp_async_elem(&ring[sl][ty + 1][33], src + cole + pz);
+      if (hs) cp_async_elem(&ring[sl][0][tx + 1], src + cols + pz);
+      if (hn) cp_async_elem(&ring[sl][BY + 1][tx + 1], src + coln + pz);
+    }
+    cp_async_commit();
+  };
+  for (int q = z0 - 1; q <= z0 + PF; ++q) issue(q);
+  for (int z = z0; z < z1; ++z) {
+    issue(z + 1 + PF);
+    cp_async_wait<PF>();
+    __syncthreads();
+    if (active) {
+      const int sb = (z - z0) % S, sc = (z - z0 + 1) % S, st = (z - z0 + 2) % S;
+      T fv = T(0);
+      if (HAS_F) fv = f[col + (int64_t)(z + 1) * sy];
+      const T v = site_update<T, Ar, HAS_F, WEIGHTED>(ring[sc][ty + 1][tx], ring[sc][ty + 1][tx + 2],
+                                                      ring[sc][ty][tx + 1], ring[sc][ty + 2][tx + 1],
+                                                      ring[sb][ty + 1][tx + 1], ring[st][ty + 1][tx + 1], fv,
+                                                      ring[sc][ty + 1][tx + 1], c);
+      dst[col + (int64_t)(z + 1) * sy] = v;
+    }
+  }
+  cp_async_wait<0>();
+}
+
 template <typename T>
 struct JacobiLaunch {
   template <class Ar, bool HAS_F, bool WEIGHTED, int BY>
-  static cudaError_t go(const T* src, T* dst, const T* f, const Geom& g, int zchunk, Coef<T> c, cudaStream_t st) {
+  static cudaError_t go(const T* src, T* dst, const T* f, const Geom& g, int zchunk, Coef<T> c, bool pipe,
+                        cudaStream_t st) {
     dim3 block(32, BY);
     dim3 grid((g.nx + 31) / 32, (g.ny + BY - 1) / BY, (g.nz + zchunk - 1) / zchunk);
-    jacobi_zmarch_kernel<T, Ar, HAS_F, WEIGHTED, BY><<<grid, block, 0, st>>>(src, dst, f, g, zchunk, c);
+    if (pipe)
+      jacobi_pipe_kernel<T, Ar, HAS_F, WEIGHTED, BY, 8><<<grid, block, 0, st>>>(src, dst, f, g, zchunk, c);
+    else
+      jacobi_zmarch_kernel<T, Ar, HAS_F, WEIGHTED, BY><<<grid, block, 0, st>>>(src, dst, f, g, zchunk, c);
     return cudaGetLastError();
   }
   template <class Ar, int BY>
   static cudaError_t pick(const T* src, T* dst, const T* f, const Geom& g, int zchunk, Coef<T> c, bool weighted,
-                          cudaStream_t st) {
+                          bool pipe, cudaStream_t st) {
     if (f) {
-      return weighted ? go<Ar, true, true, BY>(src, dst, f, g, zchunk, c, st)
-                      : go<Ar, true, false, BY>(src, dst, f, g, zchunk, c, st);
+      return weighted ? go<Ar, true, true, BY>(src, dst, f, g, zchunk, c, pipe, st)
+                      : go<Ar, true, false, BY>(src, dst, f, g, zchunk, c, pipe, st);
     }
-    return weighted ? go<Ar, false, true, BY>(src, dst, f, g, zchunk, c, st)
-                    : go<Ar, false, false, BY>(src, dst, f, g, zchunk, c, st);
+    return weighted ? go<Ar, false, true, BY>(src, dst, f, g, zchunk, c, pipe, st)
+                    : go<Ar, false, false, BY>(src, dst, f, g, zchunk, c, pipe, st);
   }
 };
 
 // One sweep src -> dst (both hold the same Dirichlet halo).
 template <typename T>
 cudaError_t jacobi_sweep(const T* src, T* dst, const T* f, const Geom& g, int by, int zchunk, Coef<T> c,
-                         bool weighted, cudaStream_t st) {
+                         bool weighted, bool pipe, cudaStream_t st) {
   using Ar = typename DefaultArith<T>::type;
   switch (by) {
-    case 4: return JacobiLaunch<T>::template pick<Ar, 4>(src, dst, f, g, zchunk, c, weighted, st);
-    case 16: return JacobiLaunch<T>::template pick<Ar, 16>(src, dst, f, g, zchunk, c, weighted, st);
-    default: return JacobiLaunch<T>::template pick<Ar, 8>(src, dst, f, g, zchunk, c, weighted, st);
+    case 4: return JacobiLaunch<T>::template pick<Ar, 4>(src, dst, f, g, zchunk, c, weighted, pipe, st);
+    case 16: return JacobiLaunch<T>::template pick<Ar, 16>(src, dst, f, g, zchunk, c, weighted, pipe, st);
+    default: return JacobiLaunch<T>::template pick<Ar, 8>(src, dst, f, g, zchunk, c, weighted, pipe, st);
   }
 }
 
 template <typename T>
 int tb_jacobi_run(stencil_ctx* ctx, T* u, T* tmp, const T* f, const Geom& g, double h, int nsweeps,
                   const stencil_params* p, cudaStream_t st);
+cudaError_t jacobi_tbz_pass(const float* src, float* dst, const float* f, const Geom& g, int levels, int by,
+                            int zchunk, Coef<float> c, cudaStream_t st);
+
+// FP32 temporal blocking on chip (tb_zmarch.cu): passes of up to nt <= 4 sweeps.
+template <typename T>
+static int tbz_run(stencil_ctx* ctx, T* u, T* tmp, const T* f, const Geom& g, double h, int nsweeps, int nt,
+                   const stencil_params* p, cudaStream_t st) {
+  if (sizeof(T) != 4) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "on-chip temporal blocking is FP32 only");
+  const int by = (p && p->tile_y) ? p->tile_y : 32;
+  if (by != 16 && by != 32) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "tile_y = %d (16 or 32)", by);
+  if (nt > 4) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "on-chip temporal blocking: nt = %d > 4", nt);
+  int zchunk = (p && p->tile_z) ? p->tile_z : 0;
+  if (zchunk <= 0) {
+    const long long cols = (long long)((g.nx + 63 - 2 * nt) / (64 - 2 * nt)) * ((g.ny + by - 1 - 2 * nt) / (by - 2 * nt));
+    const long long want = (long long)ctx->sm_count * 4;
+    const long long chunks = (want + cols - 1) / cols;
+    zchunk = (int)((g.nz + chunks - 1) / chunks);
+    if (zchunk < 32) zchunk = 32;
+  }
+  Coef<float> c;
+  c.a = 0.f;
+  c.b = (float)((p && p->b != 0.0) ? p->b : 1.0 / 6.0);
+  c.hh = (float)(h * h);
+  const int npass = (nsweeps + nt - 1) / nt;
+  T* a = (npass % 2) ? tmp : u;
+  T* b = (npass % 2) ? u : tmp;
+  int left = nsweeps;
+  for (int k = 0; k < npass; ++k) {
+    const int lv = left < nt ? left : nt;
+    cudaError_t e = jacobi_tbz_pass((const float*)a, (float*)b, (const float*)f, g, lv, by, zchunk, c, st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "jacobi_tbz_kernel launch");
+    ctx->launches++;
+    left -= lv;
+    T* sw = a; a = b; b = sw;
+  }
+  return STENCIL_OK;
+}
 
 template <typename T>
 static Coef<T> make_coef(double h, const stencil_params* p) {
@@ -126,12 +243,23 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   T* tmp = (T*)ws_get(ctx, SLOT_JACOBI_TMP, bytes, &status);
   if (!tmp) return status;
   const int nt = (p && p->nt > 0) ? p->nt : 1;
+  const bool weighted0 = p && p->a != 0.0;
+  if (p && p->variant == 4) {
+    if (weighted0) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "weighted sweeps on variant 4");
+    cudaError_t e0 = cudaMemcpyAsync(tmp, u, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e0 != cudaSuccess) return cuda_err(ctx, e0, "cudaMemcpyAsync(jacobi halo)");
+    return tbz_run<T>(ctx, u, tmp, f, g, h, nsweeps, nt, p, st);
+  }
   if (nt > 1 || (p && p->variant == 3)) {
     stencil_params q = *p;
     q.nt = nt;
     return tb_jacobi_run<T>(ctx, u, tmp, f, g, h, nsweeps, &q, st);
   }
   const bool weighted = p && p->a != 0.0;
+  // variant 1: plain z-march, 2: cp.async pipelined z-march; default: pipelined for FP32
+  const int variant = p ? p->variant : 0;
+  if (variant < 0 || variant > 4) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
+  const bool pipe = variant == 2 || (variant == 0 && sizeof(T) == 4);
   Coef<T> c = make_coef<T>(h, p);
   int by = (p && p->tile_y) ? p->tile_y : 8;
   if (by != 4 && by != 8 && by != 16)
@@ -154,7 +282,7 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   T* a = (nsweeps % 2) ? tmp : u;
   T* b = (nsweeps % 2) ? u : tmp;
   for (int s = 0; s < nsweeps; ++s) {
-    e = jacobi_sweep<T>(a, b, f, g, by, zchunk, c, weighted, st);
+    e = jacobi_sweep<T>(a, b, f, g, by, zchunk, c, weighted, pipe, st);
     ctx->launches++;
     if (e != cudaSuccess) return cuda_err(ctx, e, "jacobi_zmarch_kernel launch");
     T* sw = a; a = b; b = sw;
@@ -167,8 +295,8 @@ template int jacobi_run<double>(stencil_ctx*, double*, const double*, const Geom
 template int jacobi_run<float>(stencil_ctx*, float*, const float*, const Geom&, double, int, const stencil_params*,
                                cudaStream_t);
 template cudaError_t jacobi_sweep<double>(const double*, double*, const double*, const Geom&, int, int, Coef<double>,
-                                          bool, cudaStream_t);
+                                          bool, bool, cudaStream_t);
 template cudaError_t jacobi_sweep<float>(const float*, float*, const float*, const Geom&, int, int, Coef<float>, bool,
-                                         cudaStream_t);
+                                         bool, cudaStream_t);
 
 }  // namespace stn

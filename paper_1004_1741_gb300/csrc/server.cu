@@ -2,7 +2,8 @@
 // paper; it serves the smoothers to many concurrent users of one GPU).
 //
 // A worker thread owns the GPU work.  Each round it (1) admits waiting
-// requests in arrival order while their device memory fits the HBM budget,
+// requests in arrival order while their device memory fits the HBM budget
+// and a slot is free,
 // copying their grids to the device, where they stay until the request
 // completes; (2) runs up to `sweeps_per_round` sweeps of every admitted
 // request, all requests of one (smoother, dtype) class in ONE persistent
@@ -51,6 +52,7 @@ struct stencil_server {
   stencil_ctx* ctx = nullptr;
   size_t budget = 0;
   int quantum = 10;
+  int max_active = 0;  // slots: admitted requests at most (0 = memory bound only)
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> waiting;
@@ -102,6 +104,7 @@ static bool server_round(stencil_server* s) {
         continue;
       }
       if (s->budget && s->in_use + q->bytes > s->budget) break;  // wait, in arrival order, for memory
+      if (s->max_active && (int)s->active.size() >= s->max_active) break;  // ... or for a free slot
       s->waiting.pop_front();
       s->in_use += q->bytes;
       s->peak = std::max(s->peak, s->in_use);
@@ -252,8 +255,9 @@ static void server_main(stencil_server* s) {
 
 extern "C" {
 
-int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_bytes, int sweeps_per_round) {
-  if (!out || sweeps_per_round < 0) return STENCIL_ERR_ARG;
+int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_bytes, int sweeps_per_round,
+                          int max_active) {
+  if (!out || sweeps_per_round < 0 || max_active < 0) return STENCIL_ERR_ARG;
   *out = nullptr;
   stencil_ctx* ctx = nullptr;
   int rc = stencil_create(&ctx, device, 0);
@@ -267,6 +271,7 @@ int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_by
   s->ctx = ctx;
   s->budget = hbm_budget_bytes;
   s->quantum = sweeps_per_round > 0 ? sweeps_per_round : 10;
+  s->max_active = max_active;
   s->worker = std::thread(server_main, s);
   *out = s;
   return STENCIL_OK;

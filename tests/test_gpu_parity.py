@@ -66,6 +66,17 @@ def test_jacobi_f64_ragged(ctx, dims, nsweeps, poisson):
     _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, h, nsweeps), oracle.jacobi(u0, f0, h, nsweeps), "jacobi f64")
 
 
+@pytest.mark.parametrize("dims", RAGGED)
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_jacobi_zmarch_variants(ctx, dims, variant, dtype):
+    """Plain and cp.async-pipelined z-march, odd and even sweep counts, chunks."""
+    u0, f0 = W.random_grid(*dims, seed=7, dtype=dtype, with_f=True)
+    for ns, tile in ((3, (0, 0, 0)), (4, (32, 16, 5)), (1, (32, 4, 2))):
+        _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.3, ns, tile=tile, variant=variant),
+                      oracle.jacobi(u0, f0, 0.3, ns), "variant %d %s %s" % (variant, dims, tile))
+
+
 @pytest.mark.parametrize("tile", [(32, 4, 7), (32, 16, 3), (0, 8, 1), (0, 0, 0)])
 def test_jacobi_f64_tiles_and_zchunks(ctx, tile):
     u0, f0 = W.random_grid(45, 38, 29, seed=5, with_f=True)
@@ -104,6 +115,17 @@ def test_jacobi_temporal_f32_and_weighted(ctx, nt):
     a, b = 0.2, 0.8 / 6.0
     _assert_exact(_run(ctx, capi.stencil_jacobi, u1, f1, 0.1, ns, nt=nt, a=a, b=b),
                   oracle.jacobi(u1, f1, 0.1, ns, a=a, b=b), "weighted temporal")
+
+
+@pytest.mark.parametrize("nt", [1, 2, 3, 4])
+@pytest.mark.parametrize("by", [16, 32])
+@pytest.mark.parametrize("dims", [(45, 38, 29), (130, 70, 41), (1, 1, 9), (9, 1, 1), (64, 17, 5)])
+def test_jacobi_onchip_temporal_f32(ctx, nt, by, dims):
+    """variant 4: nt levels per pass in registers/shared memory, overlapped tiles (FP32)."""
+    u0, f0 = W.random_grid(*dims, seed=nt + by, dtype=np.float32, with_f=True)
+    for ns, zc in ((2 * nt + 1, 0), (nt, 7), (3 * nt, 40)):
+        _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.05, ns, nt=nt, tile=(0, by, zc), variant=4),
+                      oracle.jacobi(u0, f0, 0.05, ns), "onchip nt=%d by=%d %s ns=%d" % (nt, by, dims, ns))
 
 
 @pytest.mark.parametrize("dims", RAGGED)

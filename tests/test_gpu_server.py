@@ -90,3 +90,15 @@ def test_budget_admission_cancel_and_oom():
         assert res_s["status"] == capi.STENCIL_OK and np.array_equal(out, _oracle(small))
         assert srv.wait(t_big, 300)["status"] == capi.STENCIL_OK
         assert srv.stats()["hbm_peak"] <= int(nbytes * 1.5)
+
+
+def test_slot_limit_keeps_results_exact():
+    reqs = [_req(capi.STENCIL_REQ_GS if i % 2 else capi.STENCIL_REQ_JACOBI, (24 + 8 * i, 20, 16), 20 + i,
+                 sweeps=9 + i) for i in range(6)]
+    with capi.Server(0, sweeps_per_round=4, max_active=2) as srv:
+        outs = [np.empty_like(r["u"]) for r in reqs]
+        ts = [srv.submit(r["kind"], r["u"], r["f"], r["h"], r["nsweeps"], u_out=o) for r, o in zip(reqs, outs)]
+        for t in ts:
+            assert srv.wait(t, 60)["status"] == capi.STENCIL_OK
+    for r, o in zip(reqs, outs):
+        assert np.array_equal(o, _oracle(r))
