@@ -105,13 +105,21 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *  variant kernel variant: 0 = default; Gauss-Seidel 1 = tile staged in
  *          shared memory, 2 = tile updated in place through the L1 cache
  *          (one launch per tile level); 3 (both smoothers) = one persistent
- *          dataflow launch over a dependency-ordered task queue (blocking).
- *          Every variant gives the same bits. */
+ *          dataflow launch over a dependency-ordered task queue (blocking);
+ *          Jacobi 1 = z-march, 2 = z-march with asynchronous plane copies,
+ *          4 = FP32 temporal blocking on chip (nt <= 4).
+ *          Every variant gives the same bits.
+ *  int_adds FP64 only: how many of the five additions of the neighbour sum
+ *          are computed on the integer pipes (exact binary64 addition in
+ *          integer arithmetic, falling back to the FP64 pipe for operands it
+ *          does not cover): 0 = all on the FP64 pipe, 3, 4 or 5; -1 = the
+ *          library default.  Same bits whatever the value. */
 typedef struct stencil_params {
   int nt;
   int tile_x, tile_y, tile_z;
   double a, b;
   int variant;
+  int int_adds;
 } stencil_params;
 
 /* Jacobi smoother (Sec. 3, first listing; temporal blocking Sec. 4).
@@ -247,6 +255,14 @@ int stencil_server_cancel(stencil_server* srv, uint64_t ticket);
 int stencil_server_stats_get(stencil_server* srv, stencil_server_stats* out);
 /* Stops the worker after the current round and frees everything. */
 void stencil_server_destroy(stencil_server* srv);
+
+/* Self-check of the integer-pipe binary64 addition: n pairs drawn from a
+ * counter-based generator seeded by `seed` (random magnitudes, ties, carries,
+ * zeros, signs), each summed on the integer pipes and on the FP64 pipe.
+ * *out_mismatch (host) receives the number of pairs whose bits differ (must
+ * be 0), *out_fast the number the integer path handled.  Blocking. */
+int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t seed, uint64_t* out_mismatch,
+                             uint64_t* out_fast);
 
 /* residual_norm without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc when they

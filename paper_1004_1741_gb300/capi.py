@@ -46,7 +46,7 @@ class StencilError(RuntimeError):
 
 class stencil_params(ctypes.Structure):
     _fields_ = [("nt", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
-                ("a", ctypes.c_double), ("b", ctypes.c_double), ("variant", ctypes.c_int)]
+                ("a", ctypes.c_double), ("b", ctypes.c_double), ("variant", ctypes.c_int), ("int_adds", ctypes.c_int)]
 
 
 class stencil_request(ctypes.Structure):
@@ -103,6 +103,8 @@ _SIGS = {
     "stencil_server_cancel": (_I, [_P, ctypes.c_uint64]),
     "stencil_server_stats_get": (_I, [_P, ctypes.POINTER(stencil_server_stats)]),
     "stencil_server_destroy": (None, [_P]),
+    "stencil_selftest_int_add": (_I, [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
     "residual_norm_noalloc": (_I, [_P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stencil_solve_mixed": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
     "stencil_solve_f64": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, _PP, ctypes.POINTER(_D), ctypes.POINTER(_I),
@@ -167,10 +169,11 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _params(nt=0, tile=(0, 0, 0), a=0.0, b=0.0, variant=0):
+def _params(nt=0, tile=(0, 0, 0), a=0.0, b=0.0, variant=0, int_adds=-1):
     p = stencil_params()
     p.nt, p.tile_x, p.tile_y, p.tile_z, p.a, p.b = int(nt), int(tile[0]), int(tile[1]), int(tile[2]), float(a), float(b)
     p.variant = int(variant)
+    p.int_adds = int(int_adds)
     return p
 
 
@@ -224,10 +227,11 @@ class Context:
 
 # ------------------------------------------------------------ entry points --
 def stencil_jacobi(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int, *, nt: int = 0,
-                   tile=(0, 0, 0), a: float = 0.0, b: float = 0.0, variant: int = 0, stream=None) -> None:
+                   tile=(0, 0, 0), a: float = 0.0, b: float = 0.0, variant: int = 0, int_adds: int = -1,
+                   stream=None) -> None:
     """Jacobi sweeps in place on u (FP64 or FP32 by u's dtype)."""
     lib = load_library()
-    p = _params(nt, tile, a, b, variant)
+    p = _params(nt, tile, a, b, variant, int_adds)
     if u.dtype == torch.float64:
         rc = lib.stencil_jacobi_ex(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
                                    float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
@@ -238,10 +242,10 @@ def stencil_jacobi(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: flo
 
 
 def stencil_gs_lex(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int, *, nt: int = 0,
-                   tile=(0, 0, 0), variant: int = 0, stream=None) -> None:
+                   tile=(0, 0, 0), variant: int = 0, int_adds: int = -1, stream=None) -> None:
     """Lexicographic Gauss-Seidel sweeps in place on u (FP64 or FP32 by u's dtype)."""
     lib = load_library()
-    p = _params(nt, tile, variant=variant)
+    p = _params(nt, tile, variant=variant, int_adds=int_adds)
     if u.dtype == torch.float64:
         rc = lib.stencil_gs_lex_ex(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
                                    float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
@@ -285,6 +289,14 @@ def stencil_batched(ctx: Context, us, fs, hs, nsweeps, smoother: int, *, nt: int
     rc = lib.stencil_batched(ctx.handle, n, up, fp, dims, hh, ns, int(smoother), dtype, ctypes.byref(p),
                              _stream(stream))
     _check(ctx, rc)
+
+
+def stencil_selftest_int_add(ctx: Context, n: int, seed: int = 1):
+    """Returns (mismatches, handled on the integer pipes) over n generated pairs."""
+    mm, fast = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(ctx, load_library().stencil_selftest_int_add(ctx.handle, int(n), int(seed), ctypes.byref(mm),
+                                                        ctypes.byref(fast)))
+    return mm.value, fast.value
 
 
 def stencil_set_wait_limit(ctx: Context, timeout_ns: int, never_publish: int = -1) -> None:

@@ -281,6 +281,10 @@ static int gs_levels(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> 
   return STENCIL_OK;
 }
 
+template <typename T, class Ar>
+static int gs_tiles(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz, int nt,
+                    int nsweeps, bool direct, cudaStream_t st);
+
 template <typename T>
 int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps, const stencil_params* p,
            cudaStream_t st) {
@@ -310,8 +314,21 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
   c.a = T(0);
   c.b = (T)((p && p->b != 0.0) ? p->b : 1.0 / 6.0);
   c.hh = (T)(h * h);
+  const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAdds;
+  if (int_adds != 0 && int_adds != 3 && int_adds != 4 && int_adds != 5)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0, 3, 4, 5)", int_adds);
+  if constexpr (sizeof(T) == 8) {
+    if (int_adds == 3) return gs_tiles<T, ArithF64Mix<0x12u>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
+    if (int_adds == 4) return gs_tiles<T, ArithF64Mix<0x10u>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
+    if (int_adds == 5) return gs_tiles<T, ArithF64Mix<0x00u>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
+  }
+  return gs_tiles<T, typename DefaultArith<T>::type>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
+}
+
+template <typename T, class Ar>
+static int gs_tiles(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz, int nt,
+                    int nsweeps, bool direct, cudaStream_t st) {
   TileGeom tg;
-  using Ar = typename DefaultArith<T>::type;
   int rc;
 #define GS_TILE(WW, HH, DD)                                                              \
   if (tx == WW && ty == HH && tz == DD) {                                                \

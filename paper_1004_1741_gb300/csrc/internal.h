@@ -84,6 +84,11 @@ int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Ge
 int correct_launch(stencil_ctx* ctx, double* u, const float* e, const Geom& g, cudaStream_t st);
 
 constexpr int STENCIL_UNSUPPORTED_TILE = 1;
+// default number of FP64 neighbour-sum additions done on the integer pipes:
+// the Jacobi z-march gains from moving three of five off the FP64 pipe
+// (measured 81 -> 89 GLUP/s at 400^3), the Gauss-Seidel tasks do not
+constexpr int kDefaultIntAdds = 0;
+constexpr int kDefaultIntAddsJacobi = 3;
 void dataflow_release(stencil_ctx* ctx);  // internal: no kernel instantiated for a tile shape
 
 // Persistent dataflow run of the skewed-tile schedule over n grids (dataflow.cu).

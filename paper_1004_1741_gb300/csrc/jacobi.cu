@@ -172,15 +172,29 @@ struct JacobiLaunch {
 };
 
 // One sweep src -> dst (both hold the same Dirichlet halo).
-template <typename T>
-cudaError_t jacobi_sweep(const T* src, T* dst, const T* f, const Geom& g, int by, int zchunk, Coef<T> c,
-                         bool weighted, bool pipe, cudaStream_t st) {
-  using Ar = typename DefaultArith<T>::type;
+template <typename T, class Ar>
+static cudaError_t jacobi_sweep_ar(const T* src, T* dst, const T* f, const Geom& g, int by, int zchunk, Coef<T> c,
+                                   bool weighted, bool pipe, cudaStream_t st) {
   switch (by) {
     case 4: return JacobiLaunch<T>::template pick<Ar, 4>(src, dst, f, g, zchunk, c, weighted, pipe, st);
     case 16: return JacobiLaunch<T>::template pick<Ar, 16>(src, dst, f, g, zchunk, c, weighted, pipe, st);
     default: return JacobiLaunch<T>::template pick<Ar, 8>(src, dst, f, g, zchunk, c, weighted, pipe, st);
   }
+}
+
+// int_adds: additions of the neighbour sum done on the integer pipes (FP64 only; 0, 3, 4 or 5).
+template <typename T>
+cudaError_t jacobi_sweep(const T* src, T* dst, const T* f, const Geom& g, int by, int zchunk, Coef<T> c,
+                         bool weighted, bool pipe, int int_adds, cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    switch (int_adds) {
+      case 3: return jacobi_sweep_ar<T, ArithF64Mix<0x12u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
+      case 4: return jacobi_sweep_ar<T, ArithF64Mix<0x10u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
+      case 5: return jacobi_sweep_ar<T, ArithF64Mix<0x00u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
+      default: break;
+    }
+  }
+  return jacobi_sweep_ar<T, typename DefaultArith<T>::type>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
 }
 
 template <typename T>
@@ -260,6 +274,9 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   const int variant = p ? p->variant : 0;
   if (variant < 0 || variant > 4) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
   const bool pipe = variant == 2 || (variant == 0 && sizeof(T) == 4);
+  const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsJacobi;
+  if (int_adds != 0 && int_adds != 3 && int_adds != 4 && int_adds != 5)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0, 3, 4, 5)", int_adds);
   Coef<T> c = make_coef<T>(h, p);
   int by = (p && p->tile_y) ? p->tile_y : 8;
   if (by != 4 && by != 8 && by != 16)
@@ -282,7 +299,7 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   T* a = (nsweeps % 2) ? tmp : u;
   T* b = (nsweeps % 2) ? u : tmp;
   for (int s = 0; s < nsweeps; ++s) {
-    e = jacobi_sweep<T>(a, b, f, g, by, zchunk, c, weighted, pipe, st);
+    e = jacobi_sweep<T>(a, b, f, g, by, zchunk, c, weighted, pipe, int_adds, st);
     ctx->launches++;
     if (e != cudaSuccess) return cuda_err(ctx, e, "jacobi_zmarch_kernel launch");
     T* sw = a; a = b; b = sw;
@@ -295,8 +312,8 @@ template int jacobi_run<double>(stencil_ctx*, double*, const double*, const Geom
 template int jacobi_run<float>(stencil_ctx*, float*, const float*, const Geom&, double, int, const stencil_params*,
                                cudaStream_t);
 template cudaError_t jacobi_sweep<double>(const double*, double*, const double*, const Geom&, int, int, Coef<double>,
-                                          bool, bool, cudaStream_t);
+                                          bool, bool, int, cudaStream_t);
 template cudaError_t jacobi_sweep<float>(const float*, float*, const float*, const Geom&, int, int, Coef<float>, bool,
-                                         bool, cudaStream_t);
+                                         bool, int, cudaStream_t);
 
 }  // namespace stn

@@ -174,6 +174,32 @@ def test_gs_laplace_config1(ctx):
     _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, None, 1.0, 10), oracle.gs_lex(u0, None, 1.0, 10), "gs config1")
 
 
+# ------------------------------------------ FP64 additions on the integer pipes --
+def test_int_add_selftest(ctx):
+    """The integer-pipe binary64 addition equals the FP64 pipe on 2^26 generated pairs
+    (random magnitudes, near-equal operands with ties and carries, raw bit patterns)."""
+    mism, fast = capi.stencil_selftest_int_add(ctx, 1 << 26, seed=12345)
+    assert mism == 0
+    assert fast > (1 << 24)
+
+
+@pytest.mark.parametrize("int_adds", [3, 4, 5])
+@pytest.mark.parametrize("smoother", ["jacobi", "gs"])
+@pytest.mark.parametrize("dims", [(37, 19, 23), (64, 17, 5), (1, 1, 9)])
+def test_int_adds_bit_exact(ctx, int_adds, smoother, dims):
+    """Same bits whatever share of the additions runs on the integer pipes, for
+    Laplace (all operands positive: the integer path) and Poisson (signs mixed:
+    fallbacks to the FP64 pipe)."""
+    fn, ofn = (capi.stencil_jacobi, oracle.jacobi) if smoother == "jacobi" else (capi.stencil_gs_lex, oracle.gs_lex)
+    for poisson in (False, True):
+        u0, f0 = W.random_grid(*dims, seed=int_adds, with_f=poisson)
+        _assert_exact(_run(ctx, fn, u0, f0, 0.1, 5, int_adds=int_adds), ofn(u0, f0, 0.1, 5),
+                      "%s int_adds=%d poisson=%s" % (smoother, int_adds, poisson))
+    z0 = np.zeros((dims[2] + 2, dims[1] + 2, dims[0] + 2))  # zeros everywhere: the +0 operand case
+    z0[0] = 0.75
+    _assert_exact(_run(ctx, fn, z0, None, 1.0, 4, int_adds=int_adds), ofn(z0, None, 1.0, 4), "zeros")
+
+
 # ------------------------------------------------- persistent dataflow kernel --
 @pytest.mark.parametrize("smoother", ["gs", "jacobi"])
 @pytest.mark.parametrize("nt", [1, 2, 4])
