@@ -150,6 +150,16 @@ int stencil_gs_lex_ex(stencil_ctx* ctx, double* u, const double* f, const int64_
 int stencil_gs_lex_f32(stencil_ctx* ctx, float* u, const float* f, const int64_t dims[3], double h,
                        int nsweeps, const stencil_params* params, void* stream);
 
+/* Red-black Gauss-Seidel (Sec. 3 names it as the usual parallel alternative
+ * to the lexicographic order): each sweep updates all sites with (i+j+k)
+ * even, then all with (i+j+k) odd (0-based interior coordinates), in place,
+ * with the same site update.  u, f, dims, h, nsweeps as stencil_gs_lex;
+ * params may be NULL (only b is used).  Two launches per sweep. */
+int stencil_gs_rb(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h, int nsweeps,
+                  const stencil_params* params, void* stream);
+int stencil_gs_rb_f32(stencil_ctx* ctx, float* u, const float* f, const int64_t dims[3], double h, int nsweeps,
+                      const stencil_params* params, void* stream);
+
 /* Residual r = f - A u, A u = (6 u - S) * (1/(h*h)), on the interior (not in
  * the paper; the defect of -Lap_h u = f).  f may be NULL (f = 0).
  * r_out (device, same padded shape, may be NULL): receives r on the

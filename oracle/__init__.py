@@ -51,12 +51,13 @@ def _lib():
         lib.oracle_jacobi_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _D, _D, _I]
         lib.oracle_gs_lex_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _D, _I]
         lib.oracle_gs_rb_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _D, _I]
+        lib.oracle_gs_rb_f32.argtypes = [_P, _P, _I64, _I64, _I64, _D, _F, _I]
         lib.oracle_residual_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _P, _P, _P]
         lib.oracle_jacobi_f32.argtypes = [_P, _P, _I64, _I64, _I64, _D, _F, _F, _I]
         lib.oracle_gs_lex_f32.argtypes = [_P, _P, _I64, _I64, _I64, _D, _F, _I]
         lib.oracle_solve_mixed.argtypes = [_P, _P, _I64, _I64, _I64, _D, _I, _D, _I, _I, _P, _P]
         lib.oracle_solve_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _I, _D, _I, _I, _P, _P]
-        for name in ("oracle_jacobi_f64", "oracle_gs_lex_f64", "oracle_gs_rb_f64", "oracle_residual_f64",
+        for name in ("oracle_jacobi_f64", "oracle_gs_lex_f64", "oracle_gs_rb_f64", "oracle_gs_rb_f32", "oracle_residual_f64",
                      "oracle_jacobi_f32", "oracle_gs_lex_f32", "oracle_solve_mixed", "oracle_solve_f64"):
             getattr(lib, name).restype = _I
         _LIB = lib
@@ -122,8 +123,15 @@ def gs_lex(u: np.ndarray, f: np.ndarray | None = None, h: float = 1.0, nsweeps: 
 
 
 def gs_rb(u: np.ndarray, f: np.ndarray | None = None, h: float = 1.0, nsweeps: int = 1) -> np.ndarray:
-    """Return u after ``nsweeps`` red-black Gauss-Seidel sweeps (red = (i+j+k) even first), FP64."""
+    """Return u after ``nsweeps`` red-black Gauss-Seidel sweeps (red = (i+j+k) even first,
+    0-based interior coordinates); float64 or float32 by u's dtype."""
     out = np.array(u, copy=True, order="C")
+    if out.dtype == np.float32:
+        _check(out, f, np.float32)
+        rc = _lib().oracle_gs_rb_f32(_ptr(out), _ptr(f), *_dims(out), h, B32, nsweeps)
+        if rc != 0:
+            raise RuntimeError("oracle_gs_rb rc=%d" % rc)
+        return out
     _check(out, f, np.float64)
     rc = _lib().oracle_gs_rb_f64(_ptr(out), _ptr(f), *_dims(out), h, B64, nsweeps)
     if rc != 0:

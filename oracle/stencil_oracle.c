@@ -248,6 +248,24 @@ int oracle_gs_lex_f32(float* u, const float* f, int64_t nx, int64_t ny, int64_t 
   return ORC_OK;
 }
 
+/* Red-black Gauss-Seidel in single precision (same order as the FP64 one). */
+int oracle_gs_rb_f32(float* u, const float* f, int64_t nx, int64_t ny, int64_t nz, double h, float b,
+                     int nsweeps) {
+  orc_grid g;
+  if (!u || nsweeps < 0 || orc_grid_make(&g, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  const float hh = (float)(h * h);
+  for (int it = 0; it < nsweeps; ++it)
+    for (int colour = 0; colour < 2; ++colour)
+      for (int64_t k = 0; k < nz; ++k)
+        for (int64_t j = 0; j < ny; ++j)
+          for (int64_t i = 0; i < nx; ++i) {
+            if (((i + j + k) & 1) != colour) continue;
+            size_t c = orc_at(&g, i, j, k);
+            u[c] = orc_site_s(u, f, c, g.sx, g.sy, 0.0f, b, hh);
+          }
+  return ORC_OK;
+}
+
 /* ---------------------------------------------------------------------------
  * Defect correction with FP32 inner sweeps.
  *

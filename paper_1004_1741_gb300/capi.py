@@ -91,6 +91,8 @@ _SIGS = {
     "stencil_gs_lex": (_I, [_P, _P, _P, _I64P, _D, _I, _P]),
     "stencil_gs_lex_ex": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
     "stencil_gs_lex_f32": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
+    "stencil_gs_rb": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
+    "stencil_gs_rb_f32": (_I, [_P, _P, _P, _I64P, _D, _I, _PP, _P]),
     "residual_norm": (_I, [_P, _P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stencil_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I64P, ctypes.POINTER(_D),
                              ctypes.POINTER(_I), _I, _I, _PP, _P]),
@@ -252,6 +254,20 @@ def stencil_gs_lex(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: flo
     else:
         rc = lib.stencil_gs_lex_f32(ctx.handle, _grid(u, torch.float32), _opt_grid(f, u, torch.float32), _dims(u),
                                     float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
+    _check(ctx, rc)
+
+
+def stencil_gs_rb(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int,
+                  stream=None) -> None:
+    """Red-black Gauss-Seidel sweeps in place on u (FP64 or FP32 by u's dtype)."""
+    lib = load_library()
+    p = _params()
+    if u.dtype == torch.float64:
+        rc = lib.stencil_gs_rb(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u), float(h),
+                               int(nsweeps), ctypes.byref(p), _stream(stream))
+    else:
+        rc = lib.stencil_gs_rb_f32(ctx.handle, _grid(u, torch.float32), _opt_grid(f, u, torch.float32), _dims(u),
+                                   float(h), int(nsweeps), ctypes.byref(p), _stream(stream))
     _check(ctx, rc)
 
 

@@ -258,6 +258,16 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   if (!tmp) return status;
   const int nt = (p && p->nt > 0) ? p->nt : 1;
   const bool weighted0 = p && p->a != 0.0;
+  // FP32 with 2..4 sweeps per pass: on-chip temporal blocking is the default
+  const bool tbz_default = sizeof(T) == 4 && (!p || p->variant == 0) && nt >= 2 && nt <= 4 && !weighted0;
+  if (tbz_default) {
+    cudaError_t e0 = cudaMemcpyAsync(tmp, u, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e0 != cudaSuccess) return cuda_err(ctx, e0, "cudaMemcpyAsync(jacobi halo)");
+    stencil_params q = p ? *p : stencil_params{};
+    if (!q.tile_y) q.tile_y = 16;
+    if (!q.tile_z) q.tile_z = 64;
+    return tbz_run<T>(ctx, u, tmp, f, g, h, nsweeps, nt, &q, st);
+  }
   if (p && p->variant == 4) {
     if (weighted0) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "weighted sweeps on variant 4");
     cudaError_t e0 = cudaMemcpyAsync(tmp, u, bytes, cudaMemcpyDeviceToDevice, st);
@@ -270,10 +280,10 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
     return tb_jacobi_run<T>(ctx, u, tmp, f, g, h, nsweeps, &q, st);
   }
   const bool weighted = p && p->a != 0.0;
-  // variant 1: plain z-march, 2: cp.async pipelined z-march; default: pipelined for FP32
+  // variant 1: plain z-march (default), 2: z-march with asynchronous plane copies
   const int variant = p ? p->variant : 0;
   if (variant < 0 || variant > 4) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
-  const bool pipe = variant == 2 || (variant == 0 && sizeof(T) == 4);
+  const bool pipe = variant == 2;
   const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsJacobi;
   if (int_adds != 0 && int_adds != 3 && int_adds != 4 && int_adds != 5)
     return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0, 3, 4, 5)", int_adds);

@@ -218,10 +218,23 @@ int stencil_solve_mixed(stencil_ctx* ctx, double* u, const double* f, const int6
   while (rel > rtol && it < max_outer) {
     e = cudaMemsetAsync(e32, 0, n * sizeof(float), st);
     if (e != cudaSuccess) return cuda_err(ctx, e, "memset e32");
-    if (smoother == STENCIL_JACOBI)
-      rc = jacobi_run<float>(ctx, e32, r32, g, h, inner_sweeps, nullptr, st);
-    else
-      rc = gs_run<float>(ctx, e32, r32, g, h, inner_sweeps, nullptr, st);
+    // FP32 inner sweeps: Jacobi with on-chip temporal blocking (3 sweeps per
+    // pass), Gauss-Seidel with 4 sweeps per task on 32x8x8 skewed tiles
+    stencil_params q{};
+    q.int_adds = -1;
+    if (smoother == STENCIL_JACOBI) {
+      q.variant = 4;
+      q.nt = 3;
+      q.tile_y = 16;
+      q.tile_z = 64;
+      rc = jacobi_run<float>(ctx, e32, r32, g, h, inner_sweeps, &q, st);
+    } else {
+      q.nt = inner_sweeps >= 4 ? 4 : 1;
+      q.tile_x = 32;
+      q.tile_y = 8;
+      q.tile_z = 8;
+      rc = gs_run<float>(ctx, e32, r32, g, h, inner_sweeps, &q, st);
+    }
     if (rc) return rc;
     if ((rc = correct_launch(ctx, u, e32, g, st))) return rc;
     ++it;

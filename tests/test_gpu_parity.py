@@ -264,6 +264,15 @@ def test_autotune_picks_a_valid_config(ctx, smoother):
     _assert_exact(_run(ctx, fn, u0, f0, 0.02, 8, **params), ofn(u0, f0, 0.02, 8), "autotuned %s" % params)
 
 
+# ---------------------------------------------------------- red-black GS --
+@pytest.mark.parametrize("dims", RAGGED)
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_gs_red_black(ctx, dims, dtype):
+    u0, f0 = W.random_grid(*dims, seed=31, dtype=dtype, with_f=True)
+    for ns in (1, 4):
+        _assert_exact(_run(ctx, capi.stencil_gs_rb, u0, f0, 0.2, ns), oracle.gs_rb(u0, f0, 0.2, ns), "rb %s" % (dims,))
+
+
 # ---------------------------------------------------------------- residual --
 @pytest.mark.parametrize("dims", [(37, 19, 23), (1, 1, 1), (64, 64, 64)])
 def test_residual_norm(ctx, dims):

@@ -128,6 +128,17 @@ def test_gs_red_black_half_sweeps():
     np.testing.assert_allclose(F.interior(oracle.gs_rb(u, None, 1.0, 1)), x, rtol=16 * EPS)
 
 
+def test_gs_red_black_f32_matches_f64_within_single_precision():
+    nx, ny, nz = 6, 5, 4
+    rng = np.random.default_rng(10)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    out32 = oracle.gs_rb(u.astype(np.float32), f.astype(np.float32), 0.2, 3)
+    out64 = oracle.gs_rb(u, f, 0.2, 3)
+    assert out32.dtype == np.float32
+    np.testing.assert_allclose(out32.astype(np.float64), out64, rtol=0, atol=64 * EPS32)
+
+
 # ------------------------------------------------- schedules (exactness) ----
 @pytest.mark.parametrize("dims", [(4, 4, 4), (5, 3, 6), (1, 1, 5), (6, 2, 1)])
 def test_gs_hyperplane_order_is_bit_exact(dims):
