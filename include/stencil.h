@@ -112,8 +112,8 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *  int_adds FP64 only: how many of the five additions of the neighbour sum
  *          are computed on the integer pipes (exact binary64 addition in
  *          integer arithmetic, falling back to the FP64 pipe for operands it
- *          does not cover): 0 = all on the FP64 pipe, 3, 4 or 5; -1 = the
- *          library default.  Same bits whatever the value. */
+ *          does not cover): 0 = all on the FP64 pipe ... 5 = all five on
+ *          the integer pipes; -1 = the library default.  Same bits whatever the value. */
 typedef struct stencil_params {
   int nt;
   int tile_x, tile_y, tile_z;

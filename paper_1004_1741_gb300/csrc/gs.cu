@@ -315,9 +315,11 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
   c.b = (T)((p && p->b != 0.0) ? p->b : 1.0 / 6.0);
   c.hh = (T)(h * h);
   const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAdds;
-  if (int_adds != 0 && int_adds != 3 && int_adds != 4 && int_adds != 5)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0, 3, 4, 5)", int_adds);
+  if (int_adds < 0 || int_adds > 5)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
   if constexpr (sizeof(T) == 8) {
+    if (int_adds == 1) return gs_tiles<T, ArithF64Mix<0x1Du>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
+    if (int_adds == 2) return gs_tiles<T, ArithF64Mix<0x15u>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
     if (int_adds == 3) return gs_tiles<T, ArithF64Mix<0x12u>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
     if (int_adds == 4) return gs_tiles<T, ArithF64Mix<0x10u>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
     if (int_adds == 5) return gs_tiles<T, ArithF64Mix<0x00u>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);

@@ -84,11 +84,12 @@ int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Ge
 int correct_launch(stencil_ctx* ctx, double* u, const float* e, const Geom& g, cudaStream_t st);
 
 constexpr int STENCIL_UNSUPPORTED_TILE = 1;
-// default number of FP64 neighbour-sum additions done on the integer pipes:
-// the Jacobi z-march gains from moving three of five off the FP64 pipe
-// (measured 81 -> 89 GLUP/s at 400^3), the Gauss-Seidel tasks do not
-constexpr int kDefaultIntAdds = 0;
-constexpr int kDefaultIntAddsJacobi = 3;
+// default number of FP64 neighbour-sum additions done on the integer pipes,
+// the balance of the FP64 pipe against the (half-rate) integer ALU pipe
+// measured at 400^3: Jacobi z-march 81 GLUP/s at 0, 96 at 1, 114 at 2, 89 at 3;
+// Gauss-Seidel tasks 66 at 0, 71 at 1, 70.5 at 2
+constexpr int kDefaultIntAdds = 1;
+constexpr int kDefaultIntAddsJacobi = 2;
 void dataflow_release(stencil_ctx* ctx);  // internal: no kernel instantiated for a tile shape
 
 // Persistent dataflow run of the skewed-tile schedule over n grids (dataflow.cu).

@@ -188,6 +188,8 @@ cudaError_t jacobi_sweep(const T* src, T* dst, const T* f, const Geom& g, int by
                          bool weighted, bool pipe, int int_adds, cudaStream_t st) {
   if constexpr (sizeof(T) == 8) {
     switch (int_adds) {
+      case 1: return jacobi_sweep_ar<T, ArithF64Mix<0x1Du>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
+      case 2: return jacobi_sweep_ar<T, ArithF64Mix<0x15u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
       case 3: return jacobi_sweep_ar<T, ArithF64Mix<0x12u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
       case 4: return jacobi_sweep_ar<T, ArithF64Mix<0x10u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
       case 5: return jacobi_sweep_ar<T, ArithF64Mix<0x00u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
@@ -285,8 +287,8 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   if (variant < 0 || variant > 4) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
   const bool pipe = variant == 2;
   const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsJacobi;
-  if (int_adds != 0 && int_adds != 3 && int_adds != 4 && int_adds != 5)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0, 3, 4, 5)", int_adds);
+  if (int_adds < 0 || int_adds > 5)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
   Coef<T> c = make_coef<T>(h, p);
   int by = (p && p->tile_y) ? p->tile_y : 8;
   if (by != 4 && by != 8 && by != 16)

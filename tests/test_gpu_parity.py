@@ -183,7 +183,7 @@ def test_int_add_selftest(ctx):
     assert fast > (1 << 24)
 
 
-@pytest.mark.parametrize("int_adds", [3, 4, 5])
+@pytest.mark.parametrize("int_adds", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("smoother", ["jacobi", "gs"])
 @pytest.mark.parametrize("dims", [(37, 19, 23), (64, 17, 5), (1, 1, 9)])
 def test_int_adds_bit_exact(ctx, int_adds, smoother, dims):
