@@ -260,7 +260,7 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (the smoother call that took longer)
     dom = "gs" if acc["g"] >= acc["j"] else "jacobi"
-    kern = "gs_task_kernel" if dom == "gs" else "jacobi_zmarch_kernel"
+    kern = "gs_direct_kernel" if dom == "gs" else "jacobi_zmarch_kernel"
     nlaunch = (args.steps and (launch_counts(ctx, dom, cj if dom == "jacobi" else cg))) or 1
     dur_s = (acc["g"] if dom == "gs" else acc["j"]) / 1e3 / (args.steps * nlaunch)
     flops_per_launch = FP64_OPS_PER_LUP * SWEEPS * N ** 3 / nlaunch
@@ -268,7 +268,9 @@ def run_gpu(args):
     traffic = _traffic_from_profiles(kern)
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK_TOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_ALU_PEAK_TOPS, "traffic": traffic, "kernel": kern,
-                "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz (1.25 TFLOP/s FMA-counted datasheet)"}
+                "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz (1.25 TFLOP/s FMA-counted datasheet); "
+                               "achieved counts the 6 FP64 operations of a site update, some of which run on the "
+                               "integer pipes"}
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_bound = {str(nt): hbm * nt / 16.0 for nt in NT_SWEEP}
