@@ -59,12 +59,23 @@ __global__ void __launch_bounds__(32 * BY) jacobi_tbz_kernel(const T* __restrict
 #pragma unroll
     for (int l = 0; l < NT; ++l) P[k][l] = C[k][l] = N[k][l] = T(0);
   const int64_t sy = g.sy;
+  // level-0 planes are loaded PF steps before they are used (register queue)
+  constexpr int PF = 4;
+  T qv[2][PF];
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int i = 0; i < PF; ++i)
+      qv[k][i] = (valid[k] && zs + i <= ze) ? src[col[k] + (int64_t)(zs + i + 1) * sy] : T(0);
   for (int q = zs; q <= z1 - 1 + NT; ++q) {
     const int b = q & 1, bp = b ^ 1;
     // level 0: plane q
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const T v = (valid[k] && q <= ze) ? src[col[k] + (int64_t)(q + 1) * sy] : T(0);
+      const T v = qv[k][0];
+#pragma unroll
+      for (int i = 0; i + 1 < PF; ++i) qv[k][i] = qv[k][i + 1];
+      qv[k][PF - 1] = (valid[k] && q + PF <= ze) ? src[col[k] + (int64_t)(q + PF + 1) * sy] : T(0);
       P[k][0] = C[k][0];
       C[k][0] = N[k][0];
       N[k][0] = v;

@@ -72,7 +72,7 @@ def test_jacobi_f64_ragged(ctx, dims, nsweeps, poisson):
 def test_jacobi_zmarch_variants(ctx, dims, variant, dtype):
     """Plain and cp.async-pipelined z-march, odd and even sweep counts, chunks."""
     u0, f0 = W.random_grid(*dims, seed=7, dtype=dtype, with_f=True)
-    for ns, tile in ((3, (0, 0, 0)), (4, (32, 16, 5)), (1, (32, 4, 2))):
+    for ns, tile in ((3, (0, 0, 0)), (4, (32, 16, 5)), (1, (32, 4, 2)), (2, (32, 8, 1))):
         _assert_exact(_run(ctx, capi.stencil_jacobi, u0, f0, 0.3, ns, tile=tile, variant=variant),
                       oracle.jacobi(u0, f0, 0.3, ns), "variant %d %s %s" % (variant, dims, tile))
 
