@@ -138,6 +138,23 @@ def _traffic_from_profiles(kernel: str):
 
 
 # ------------------------------------------------------------------ oracle --
+def reduce_max_over_ranks(x: float, dist, device) -> float:
+    """Max of x over the ranks of the process group (x itself when dist is None).
+    The timed region of a multi-GPU run is the slowest rank's."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_glups(lup_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: updates of all ranks over the slowest rank's time."""
+    return world * lup_per_rank / (ms_max / 1e3) / 1e9
+
+
 def _oracle_sample(n: int, sweeps: int):
     """Time the CPU oracle (as it stands) on the 400^3 grid for `sweeps` Jacobi and
     `sweeps` Gauss-Seidel sweeps.  Returns (GLUP/s, seconds, LUP)."""
@@ -247,12 +264,10 @@ def run_gpu(args):
     ms = t0.elapsed_time(t1)
     launches = ctx.kernel_launches - launches0
     clk = clocks.stop()
+    ms = reduce_max_over_ranks(ms, dist, dev)
     if dist:
-        tmax = torch.tensor([ms], device=dev)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms = float(tmax.item())
         dist.barrier()
-    value = world * lup_step * args.steps / (ms / 1e3) / 1e9
+    value = whole_job_glups(lup_step * args.steps, world, ms)
 
     # per-smoother GLUP/s over the timed region
     lup_one = SWEEPS * N ** 3 * args.steps

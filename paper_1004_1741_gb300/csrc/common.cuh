@@ -51,40 +51,36 @@ struct ArithF32 {
 // Binary64 addition carried out on the integer pipes.
 //
 // The FP64 pipe of a GB300 SM retires ~1.6 lanes per clock, while its
-// integer pipes issue 128 lanes per clock, so an FP64-bound kernel leaves
-// most issue slots idle.  int_add_f64 computes the IEEE-754 round-to-nearest-
-// even sum of two doubles with 64-bit integer arithmetic when both are
-// non-negative, the larger is normal and at most 2^1022, and the smaller is
-// +0 or normal with an exponent at most 31 below (the common case for
-// smoothed fields); otherwise it reports failure and the caller uses the
-// FP64 pipe.  Method: align the significands (53 bits, implicit bit at bit
-// 62, ten guard bits) with the bits shifted out OR-ed into the lowest bit,
-// add, renormalise by at most one bit (again keeping the sticky bit), round
-// to 53 bits to nearest, ties to even, and let a carry of the rounding ripple
+// integer pipes issue far more, so an FP64-bound kernel leaves most issue
+// slots idle.  int_add_f64 computes the IEEE-754 round-to-nearest-even sum of
+// two doubles with 64-bit integer arithmetic when both are non-negative, the
+// larger is normal and below 2^1022, and the smaller is +0 or normal at most
+// 10 binades below it (the common case for neighbouring values of a smoothed
+// field); otherwise it reports failure and the caller uses the FP64 pipe.
+// Method: the significands (implicit bit at bit 62) are aligned within ten
+// guard bits, so no bit is shifted out and no sticky bit is needed; the sum is
+// rounded to 53 bits, to nearest with ties to even, by adding
+// 2^(k-1) - 1 + (bit k of the sum) before the shift by k = 10 or 11 (one more
+// when the addition carried into bit 63); a carry out of the rounding ripples
 // into the exponent field.
 __device__ __forceinline__ bool int_add_f64(double a, double b, double* out) {
   const unsigned long long A = (unsigned long long)__double_as_longlong(a);
   const unsigned long long B = (unsigned long long)__double_as_longlong(b);
-  const unsigned long long H = A > B ? A : B;  // a negative operand ends up here and fails the exponent test
-  const unsigned long long L = A > B ? B : A;
-  const unsigned eh = (unsigned)(H >> 52), el = (unsigned)(L >> 52);
+  const unsigned ea = (unsigned)(A >> 52), eb = (unsigned)(B >> 52);  // sign bit included: negatives fail below
+  const bool sw = eb > ea;
+  const unsigned long long H = sw ? B : A, L = sw ? A : B;
+  const unsigned eh = sw ? eb : ea, el = sw ? ea : eb;
   const unsigned d = eh - el;
   const bool lzero = L == 0ull;
-  if (!((eh - 1u) < 2045u && (lzero || (el >= 1u && d < 32u)))) return false;
-  const unsigned long long FRAC = 0xFFFFFFFFFFFFFull;
-  const unsigned long long MH = ((H & FRAC) << 10) | (1ull << 62);
-  const unsigned long long ML = ((L & FRAC) << 10) | (1ull << 62);
-  const unsigned dd = lzero ? 0u : d;
-  unsigned long long Ms = ML >> dd;
-  Ms |= (unsigned long long)((((unsigned)ML) & ((1u << dd) - 1u)) != 0u);  // sticky
-  unsigned long long S = MH + Ms;                                            // < 2^64
+  if (!((eh - 1u) < 2045u && (lzero || (el >= 1u && d <= 10u)))) return false;
+  const unsigned long long FRAC = 0xFFFFFFFFFFFFFull, ONE = 1ull << 52;
+  const unsigned long long MH = ((H & FRAC) | ONE) << 10;
+  const unsigned long long ML = lzero ? 0ull : ((((L & FRAC) | ONE) << 10) >> d);
+  const unsigned long long S = MH + ML;  // < 2^64
   const unsigned c = (unsigned)(S >> 63);
-  S = (S >> c) | (S & (unsigned long long)c);
-  unsigned long long M = S >> 10;
-  const unsigned rem = (unsigned)S & 1023u;
-  M += (unsigned long long)((rem > 512u) | ((rem == 512u) & ((unsigned)M & 1u)));
-  const unsigned long long R = ((unsigned long long)(eh + c - 1u) << 52) + M;
-  *out = __longlong_as_double((long long)(lzero ? H : R));
+  const unsigned k = 10u + c;
+  const unsigned long long M = (S + ((1ull << (k - 1u)) - 1ull + ((S >> k) & 1ull))) >> k;
+  *out = __longlong_as_double((long long)(((unsigned long long)(eh + c - 1u) << 52) + M));
   return true;
 }
 

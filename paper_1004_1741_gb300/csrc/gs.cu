@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(GS_THREADS) gs_task_kernel(T* __restrict__ u, 
     // A level's sites go to consecutive threads starting at a warp that rotates
     // with the level and the CTA, so small levels do not all land on warp 0 and
     // thereby on one SM sub-partition's FP64 pipe.
-    int t = tid - (((int)blockIdx.x + lv) & 7) * 32;
+    int t = tid - (((int)blockIdx.x + lv) & (GS_THREADS / 32 - 1)) * 32;
     if (t < 0) t += GS_THREADS;
     for (int e = beg + t; e < end; e += GS_THREADS) {
       const int li = tb.lis[e];
@@ -247,11 +247,46 @@ SiteTable site_table(stencil_ctx* ctx, const TileGeom& tg) {
   size_t noff = 0;
   for (int ns = 1; ns <= tg.nt; ++ns) noff += (size_t)(tg.W + tg.H + tg.D - 2 + ns);
   SiteTable t;
+  t.goff = nullptr;
   t.coords = (const uint32_t*)sb;
   t.lis = (const uint16_t*)(sb + b_sites);
   t.off = (const int*)(sb + b_sites + b_lis);
   t.base = t.off + noff;
   return t;
+}
+
+// Per-site grid offsets (relative to the tile origin) for one grid shape, so
+// that interior tasks skip the coordinate decoding; cached per (tile, nt, sx, sy).
+static int ensure_goff(stencil_ctx* ctx, const TileGeom& tg, const Geom& g, cudaStream_t st, const int** out) {
+  *out = nullptr;
+  const int64_t key[6] = {tg.W, tg.H, tg.D, tg.nt, g.sx, g.sy};
+  if ((double)g.sy * (tg.D + tg.nt) >= 2147483647.0) return STENCIL_OK;  // offsets would not fit int32
+  bool same = ctx->slots[SLOT_GS_GOFF].ptr != nullptr;
+  for (int i = 0; i < 6; ++i) same = same && ctx->goff_key[i] == key[i];
+  if (!same) {
+    // rebuild from the packed coordinates (same order as the site table)
+    std::vector<int> goff;
+    for (int ns = 1; ns <= tg.nt; ++ns) {
+      const int lo = -(ns - 1), hi = tg.W + tg.H + tg.D - 3;
+      for (int lv = lo; lv <= hi; ++lv)
+        for (int s = 0; s < ns; ++s)
+          for (int kk = 0; kk < tg.D; ++kk)
+            for (int jj = 0; jj < tg.H; ++jj) {
+              int ii = lv + s - kk - jj;
+              if (ii < 0 || ii >= tg.W) continue;
+              goff.push_back((int)((int64_t)(kk - s) * g.sy + (int64_t)(jj - s) * g.sx + (ii - s)));
+            }
+    }
+    int status;
+    int* d = (int*)ws_get(ctx, SLOT_GS_GOFF, goff.size() * sizeof(int), &status);
+    if (!d) return status;
+    cudaError_t e = cudaMemcpyAsync(d, goff.data(), goff.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "upload of site offsets");
+    for (int i = 0; i < 6; ++i) ctx->goff_key[i] = key[i];
+  }
+  *out = (const int*)ctx->slots[SLOT_GS_GOFF].ptr;
+  return STENCIL_OK;
 }
 
 template <typename T, class Ar, bool HAS_F, int W, int H, int D>
@@ -267,7 +302,11 @@ static int gs_levels(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> 
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   if (e != cudaSuccess) return cuda_err(ctx, e, "gs smem attribute");
-  const SiteTable tb = site_table(ctx, tg);
+  SiteTable tb = site_table(ctx, tg);
+  if (direct) {
+    int rc = ensure_goff(ctx, tg, g, st, &tb.goff);
+    if (rc) return rc;
+  }
   const uint64_t* slices = slices_ptr(ctx);
   const int* soff = slice_off_ptr(ctx);
   for (int L = 0; L < tg.nlevels; ++L) {

@@ -33,6 +33,7 @@ enum SlotId {
   SLOT_DF_QUEUE,         // dataflow run: grid descriptors, task queue, completion flags
   SLOT_BATCH_TMP,        // batched Jacobi: second grids
   SLOT_TUNE_GRID,        // autotuner: copy of the caller's grid
+  SLOT_GS_GOFF,          // Gauss-Seidel site offsets for one grid shape
   SLOT_COUNT
 };
 
@@ -47,6 +48,7 @@ struct stencil_ctx {
   // Gauss-Seidel geometry cache key of what SLOT_GS_SLICES / SLOT_GS_SITES hold
   int64_t gs_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<int> gs_slice_off;  // host copy of the slice prefix offsets
+  int64_t goff_key[6] = {0, 0, 0, 0, 0, 0};  // (W, H, D, nt, sx, sy) of SLOT_GS_GOFF
   int sm_count = 0;
   unsigned long long launches = 0;  // kernels this context has launched
   void* pinned = nullptr;           // small pinned host buffer for status words

@@ -12,7 +12,7 @@ struct stencil_ctx;
 namespace stn {
 
 constexpr int GS_THREADS = 256;
-constexpr int GS_MAXPOS = 8;     // box-plane positions per thread: (W+nt+1)(H+nt+1) <= 8*256
+constexpr int GS_MAXPOS = 2048 / GS_THREADS;  // box-plane positions per thread: (W+nt+1)(H+nt+1) <= 2048
 constexpr int GS_MAXLEVELS = 128;  // tile-local levels W+H+D-3+ns <= 128
 
 // Site table of the tile-local levels (built on the host, see ensure_sites).
@@ -21,6 +21,7 @@ struct SiteTable {
   const uint16_t* lis;     // shared-memory index of the site inside the staged box
   const int* off;          // level offsets, per ns one block of W+H+D-2+ns entries
   const int* base;         // base[ns]: first entry of ns's block in off
+  const int* goff;         // per site: grid offset from the tile origin for one grid shape, or nullptr
 };
 
 // Gauss-Seidel task (I, J, K, p) updated in place through the L1 cache: the
@@ -46,19 +47,29 @@ __device__ __forceinline__ void gs_task_body(T* u, const T* __restrict__ f, cons
   __syncthreads();
   for (int lv = 0; lv < nlv; ++lv) {
     const int beg = s_off[lv], end = s_off[lv + 1];
-    int t = tid - (((int)blockIdx.x + lv) & 7) * 32;
+    int t = tid - (((int)blockIdx.x + lv) & (GS_THREADS / 32 - 1)) * 32;
     if (t < 0) t += GS_THREADS;
-    for (int e = beg + t; e < end; e += GS_THREADS) {
-      const uint32_t s = tb.coords[e];
-      const int sw = (int)(s >> 24);
-      const int dx = (int)(s & 0xFF) - sw, dy = (int)((s >> 8) & 0xFF) - sw, dz = (int)((s >> 16) & 0xFF) - sw;
-      if (!full && (X0 + dx < 0 || X0 + dx >= g.nx || Y0 + dy < 0 || Y0 + dy >= g.ny || Z0 + dz < 0 ||
-                    Z0 + dz >= g.nz))
-        continue;
-      T* q = ut + ((int64_t)dz * sy + (int64_t)dy * sx + dx);
-      T fv = T(0);
-      if (HAS_F) fv = f[q - u];
-      *q = site_update<T, Ar, HAS_F, false>(q[-1], q[1], q[-sx], q[sx], q[-sy], q[sy], fv, T(0), c);
+    if (full && tb.goff) {
+      // interior task: the site's offset comes precomputed from the table
+      for (int e = beg + t; e < end; e += GS_THREADS) {
+        T* q = ut + tb.goff[e];
+        T fv = T(0);
+        if (HAS_F) fv = f[q - u];
+        *q = site_update<T, Ar, HAS_F, false>(q[-1], q[1], q[-sx], q[sx], q[-sy], q[sy], fv, T(0), c);
+      }
+    } else {
+      for (int e = beg + t; e < end; e += GS_THREADS) {
+        const uint32_t s = tb.coords[e];
+        const int sw = (int)(s >> 24);
+        const int dx = (int)(s & 0xFF) - sw, dy = (int)((s >> 8) & 0xFF) - sw, dz = (int)((s >> 16) & 0xFF) - sw;
+        if (!full && (X0 + dx < 0 || X0 + dx >= g.nx || Y0 + dy < 0 || Y0 + dy >= g.ny || Z0 + dz < 0 ||
+                      Z0 + dz >= g.nz))
+          continue;
+        T* q = ut + ((int64_t)dz * sy + (int64_t)dy * sx + dx);
+        T fv = T(0);
+        if (HAS_F) fv = f[q - u];
+        *q = site_update<T, Ar, HAS_F, false>(q[-1], q[1], q[-sx], q[sx], q[-sy], q[sy], fv, T(0), c);
+      }
     }
     __syncthreads();
   }
