@@ -35,39 +35,50 @@ __global__ void __launch_bounds__(32 * BY) jacobi_zmarch_kernel(const T* __restr
   const bool hs = (ty == 0) && (x <= g.nx);                     // row y-1 (>= -1)
   const bool hn = (ty == BY - 1) && (y + 1 <= g.ny) && (x <= g.nx);
   const int64_t sy = g.sy;
-  const int64_t col = inside ? g.at(x, y, -1) : 0;  // padded offset of (x, y) at plane -1
-  const int64_t colw = hw ? g.at(x - 1, y, -1) : 0;
-  const int64_t cole = he ? g.at(x + 1, y, -1) : 0;
-  const int64_t cols = hs ? g.at(x, y - 1, -1) : 0;
-  const int64_t coln = hn ? g.at(x, y + 1, -1) : 0;
-
-  // registers: planes z-1, z, z+1 of the own column (plane index p at offset (p+1)*sy)
-  T below = inside ? src[col + (int64_t)(z0)*sy] : T(0);
-  T cur = inside ? src[col + (int64_t)(z0 + 1) * sy] : T(0);
-  T above = inside ? src[col + (int64_t)(z0 + 2) * sy] : T(0);
-  int buf = 0;
-  for (int z = z0; z < z1; ++z) {
-    const int64_t pz = (int64_t)(z + 1) * sy;
-    sm[buf][ty + 1][tx + 1] = cur;
-    if (hw) sm[buf][ty + 1][0] = src[colw + pz];
-    if (he) sm[buf][ty + 1][33] = src[cole + pz];
-    if (hs) sm[buf][0][tx + 1] = src[cols + pz];
-    if (hn) sm[buf][BY + 1][tx + 1] = src[coln + pz];
+  // pointers at plane z (advanced by one plane per step; dereferenced only when in range)
+  const int64_t o0 = (int64_t)(z0 + 1) * sy;
+  const T* pc = src + (inside ? g.at(x, y, -1) : 0) + o0;
+  const T* pw = src + (hw ? g.at(x - 1, y, -1) : 0) + o0;
+  const T* pe = src + (he ? g.at(x + 1, y, -1) : 0) + o0;
+  const T* ps = src + (hs ? g.at(x, y - 1, -1) : 0) + o0;
+  const T* pn = src + (hn ? g.at(x, y + 1, -1) : 0) + o0;
+  const int64_t od = (inside ? g.at(x, y, -1) : 0) + o0;
+  T* pd = dst + od;
+  const T* pf = HAS_F ? f + od : nullptr;
+  T below = inside ? pc[-sy] : T(0);
+  T cur = inside ? pc[0] : T(0);
+  T above = inside ? pc[sy] : T(0);
+  auto step = [&](int z, int bf) {
+    sm[bf][ty + 1][tx + 1] = cur;
+    if (hw) sm[bf][ty + 1][0] = *pw;
+    if (he) sm[bf][ty + 1][33] = *pe;
+    if (hs) sm[bf][0][tx + 1] = *ps;
+    if (hn) sm[bf][BY + 1][tx + 1] = *pn;
     // prefetch plane z+2 (exists up to the top halo plane nz)
-    T next = (inside && z + 2 <= g.nz) ? src[col + pz + 2 * sy] : T(0);
+    const T next = (inside && z + 2 <= g.nz) ? pc[2 * sy] : T(0);
     T fv = T(0);
-    if (HAS_F && active) fv = f[col + pz];
+    if (HAS_F && active) fv = *pf;
     __syncthreads();
-    if (active) {
-      T v = site_update<T, Ar, HAS_F, WEIGHTED>(sm[buf][ty + 1][tx], sm[buf][ty + 1][tx + 2], sm[buf][ty][tx + 1],
-                                                sm[buf][ty + 2][tx + 1], below, above, fv, cur, c);
-      dst[col + pz] = v;
-    }
+    if (active)
+      *pd = site_update<T, Ar, HAS_F, WEIGHTED>(sm[bf][ty + 1][tx], sm[bf][ty + 1][tx + 2], sm[bf][ty][tx + 1],
+                                                sm[bf][ty + 2][tx + 1], below, above, fv, cur, c);
     below = cur;
     cur = above;
     above = next;
-    buf ^= 1;
+    pc += sy;
+    pw += sy;
+    pe += sy;
+    ps += sy;
+    pn += sy;
+    pd += sy;
+    if (HAS_F) pf += sy;
+  };
+  int z = z0;
+  for (; z + 1 < z1; z += 2) {  // two planes per trip: the buffer index is a constant
+    step(z, 0);
+    step(z + 1, 1);
   }
+  if (z < z1) step(z, 0);
 }
 
 // Pipelined variant: the same 2.5D z-march, but planes arrive in shared
