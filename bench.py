@@ -30,8 +30,8 @@ N = 400
 SWEEPS = 100
 # the launch configuration timed for the headline (tests/test_gpu_parity.py checks it at full size)
 HEADLINE = {
-    "jacobi": {"nt": 1, "tile": (32, 4, 0)},
-    "gs": {"nt": 4, "tile": (32, 8, 8)},
+    "jacobi": {"nt": 1, "tile": (32, 4, 0), "variant": 0},
+    "gs": {"nt": 1, "tile": (8, 8, 0), "variant": 4},
 }
 NT_SWEEP = [1, 2, 4, 8, 16]
 METRIC = "GLUP/s at 400^3 FP64 (Jacobi, GS) vs HBM roofline; batched/served vs plain, p99"
@@ -231,11 +231,13 @@ def run_gpu(args):
     def step(timed: bool):
         if timed:
             ev["j"][0].record(stream)
-        capi.stencil_jacobi(ctx, uj, None, 1.0, SWEEPS, nt=cj["nt"], tile=cj["tile"], stream=stream)
+        capi.stencil_jacobi(ctx, uj, None, 1.0, SWEEPS, nt=cj["nt"], tile=cj["tile"], variant=cj["variant"],
+                            stream=stream)
         if timed:
             ev["j"][1].record(stream)
             ev["g"][0].record(stream)
-        capi.stencil_gs_lex(ctx, ug, None, 1.0, SWEEPS, nt=cg["nt"], tile=cg["tile"], stream=stream)
+        capi.stencil_gs_lex(ctx, ug, None, 1.0, SWEEPS, nt=cg["nt"], tile=cg["tile"], variant=cg["variant"],
+                            stream=stream)
         if timed:
             ev["g"][1].record(stream)
         rj = capi.residual_norm(ctx, uj, None, 1.0, stream=stream)
@@ -275,7 +277,7 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (the smoother call that took longer)
     dom = "gs" if acc["g"] >= acc["j"] else "jacobi"
-    kern = "gs_direct_kernel" if dom == "gs" else "jacobi_zmarch_kernel"
+    kern = "gs_column_kernel" if dom == "gs" else "jacobi_zmarch_kernel"
     nlaunch = (args.steps and (launch_counts(ctx, dom, cj if dom == "jacobi" else cg))) or 1
     dur_s = (acc["g"] if dom == "gs" else acc["j"]) / 1e3 / (args.steps * nlaunch)
     flops_per_launch = FP64_OPS_PER_LUP * SWEEPS * N ** 3 / nlaunch
@@ -321,8 +323,9 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "jacobi+gs 400^3 fp64, 100 sweeps each + residual norms", "n": N,
-                       "sweeps": SWEEPS, "jacobi": {"nt": cj["nt"], "tile": list(cj["tile"])},
-                       "gs": {"nt": cg["nt"], "tile": list(cg["tile"])}, "parallelism": "replicas" if world > 1 else "1gpu",
+                       "sweeps": SWEEPS,
+                       "jacobi": {"nt": cj["nt"], "tile": list(cj["tile"]), "variant": cj["variant"]},
+                       "gs": {"nt": cg["nt"], "tile": list(cg["tile"]), "variant": cg["variant"]}, "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "inputs larger than L2 (2 x 512.6 MB vs 129 MB); no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "details": details,
@@ -343,7 +346,7 @@ def launch_counts(ctx, smoother, cfg):
     u = torch.zeros((N + 2,) * 3, dtype=torch.float64, device="cuda")
     before = ctx.kernel_launches
     fn = capi.stencil_jacobi if smoother == "jacobi" else capi.stencil_gs_lex
-    fn(ctx, u, None, 1.0, SWEEPS, nt=cfg["nt"], tile=cfg["tile"])
+    fn(ctx, u, None, 1.0, SWEEPS, nt=cfg["nt"], tile=cfg["tile"], variant=cfg["variant"])
     torch.cuda.synchronize()
     n = ctx.kernel_launches - before
     del u
@@ -360,10 +363,11 @@ def nt_sweep(ctx, capi, torch, uj, ug, stream):
         for nt in NT_SWEEP:
             try:
                 tile = cfg["tile"] if nt == cfg["nt"] else (0, 0, 0)
-                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, stream=stream)  # warm
+                variant = cfg["variant"] if nt == cfg["nt"] else 0
+                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, variant=variant, stream=stream)  # warm
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, stream=stream)
+                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, variant=variant, stream=stream)
                 b.record(stream)
                 torch.cuda.synchronize()
                 t = a.elapsed_time(b) / 1e3
@@ -427,8 +431,10 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
     def step():
         dj.copy_(hj, non_blocking=True)
         dg.copy_(hg, non_blocking=True)
-        capi.stencil_jacobi(ctx, dj, None, 1.0, SWEEPS, nt=cj["nt"], tile=cj["tile"], stream=stream)
-        capi.stencil_gs_lex(ctx, dg, None, 1.0, SWEEPS, nt=cg["nt"], tile=cg["tile"], stream=stream)
+        capi.stencil_jacobi(ctx, dj, None, 1.0, SWEEPS, nt=cj["nt"], tile=cj["tile"], variant=cj["variant"],
+                            stream=stream)
+        capi.stencil_gs_lex(ctx, dg, None, 1.0, SWEEPS, nt=cg["nt"], tile=cg["tile"], variant=cg["variant"],
+                            stream=stream)
         capi.residual_norm(ctx, dj, None, 1.0, stream=stream)
         capi.residual_norm(ctx, dg, None, 1.0, stream=stream)
         oj.copy_(dj, non_blocking=True)
@@ -463,10 +469,10 @@ def run_case(args):
     fn = capi.stencil_jacobi if args.case == "jacobi" else capi.stencil_gs_lex
     tile = tuple(int(x) for x in args.tile.split(",")) if args.tile else (0, 0, 0)
     for _ in range(args.repeat):
-        fn(ctx, u, None, 1.0, args.sweeps, nt=args.nt, tile=tile)
+        fn(ctx, u, None, 1.0, args.sweeps, nt=args.nt, tile=tile, variant=args.variant, int_adds=args.int_adds)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.case, "n": args.n, "sweeps": args.sweeps, "nt": args.nt, "repeat": args.repeat,
-                      "launches": ctx.kernel_launches}))
+                      "variant": args.variant, "int_adds": args.int_adds, "launches": ctx.kernel_launches}))
     ctx.close()
     return 0
 
@@ -599,6 +605,8 @@ def main():
     ap.add_argument("--nt", type=int, default=1)
     ap.add_argument("--tile", default="")
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--variant", type=int, default=0, help="kernel variant of the profiling case")
+    ap.add_argument("--int-adds", type=int, default=-1, help="integer-pipe additions of the profiling case")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--suite", choices=["mixed", "served"], help="a secondary workload instead of the headline")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")

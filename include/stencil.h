@@ -104,10 +104,20 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          accepted by Jacobi (weighted Jacobi, a = 1 - omega, b = omega/6).
  *  variant kernel variant: 0 = default; Gauss-Seidel 1 = tile staged in
  *          shared memory, 2 = tile updated in place through the L1 cache
- *          (one launch per tile level); 3 (both smoothers) = one persistent
+ *          (one launch per tile level), 4 = column march: nt = 1 tasks of
+ *          tile_x x tile_y columns (8x8, 8x16, 16x8) x tile_z planes, one
+ *          thread per column marching up the tile-local wavefront through a
+ *          shared-memory ring (one launch per task level);
+ *          Gauss-Seidel default: variant 4 at nt = 1 without a tile (8x8
+ *          for FP64, 16x8 for FP32, chunks of at most 100 planes),
+ *          variant 2 otherwise;
+ *          3 (both smoothers) = one persistent
  *          dataflow launch over a dependency-ordered task queue (blocking);
  *          Jacobi 1 = z-march, 2 = z-march with asynchronous plane copies,
- *          4 = FP32 temporal blocking on chip (nt <= 4).
+ *          4 = FP32 temporal blocking on chip (nt <= 4, tile_y 16 or 32).
+ *          Jacobi default: FP32 unweighted sweeps with nt <= 4 run variant 4
+ *          (at nt = 1 only when tile_y is 0); FP64, weighted and the rest
+ *          run the z-march at nt = 1 and skewed tiles at nt > 1.
  *          Every variant gives the same bits.
  *  int_adds FP64 only: how many of the five additions of the neighbour sum
  *          are computed on the integer pipes (exact binary64 addition in

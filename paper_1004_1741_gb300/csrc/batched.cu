@@ -107,6 +107,9 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
   };
   std::vector<Cand> cands;
   if (smoother == STENCIL_GS) {
+    cands.push_back({4, 1, 0, 0, 0});  // column march, per-dtype default tile
+    for (int ty : {8, 16}) cands.push_back({4, 1, 8, ty, 0});
+    cands.push_back({4, 1, 16, 8, 0});
     const int nts[] = {1, 2, 4, 8};
     const int tiles[][3] = {{16, 16, 16}, {32, 8, 8}, {32, 16, 16}};
     for (int v : {0, 3})

@@ -134,6 +134,22 @@ __device__ __forceinline__ T site_update(T w, T e, T s, T n, T bo, T t, T fv, T 
   return v;
 }
 
+// Asynchronous element copy global -> shared (cp.async, through L1) and its
+// group bookkeeping: wait until at most N of this thread's groups are pending.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Padded-grid geometry: interior (nx, ny, nz), element (x, y, z) of the
 // interior (x in [-1, nx] etc. reaching the halo) at
 // ((z+1)*(ny+2) + (y+1))*(nx+2) + (x+1).

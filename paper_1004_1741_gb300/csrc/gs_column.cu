@@ -1,0 +1,202 @@
+// Lexicographic Gauss-Seidel, one sweep per task, as a column march
+// (Sec. 3's pipelined wavefront with every thread owning one (x, y) column).
+//
+// Tasks are the nt = 1 tiles of tiles.h: box tiles TX x TY columns x D planes,
+// task (I, J, K, p) = sweep p of tile (I, J, K), level I+J+K+2p, one launch
+// per level; tasks of one level never share a face, so they run in parallel.
+// Inside a task the sites of the tile-local wavefront i+j+k = t are exactly
+// "column (i, j) at plane t-i-j": thread (i, j) marches up its column, one
+// plane per step, i+j steps behind the tile's corner column.
+//
+// The tile lives in a shared-memory ring of R plane slots, each holding the
+// tile's TY rows plus the two neighbouring rows, each row the TX columns plus
+// the two neighbouring columns.  Cell (i, j, k) (tile column i, row j, local
+// plane k; -1 and TX / TY for the neighbours) is stored in slot (k+i+j) mod R,
+// the step at which it is updated: at step t every thread reads slot t-1 (W,
+// S, B, all updated one step earlier), slot t+1 (E, N, T, not yet updated)
+// and writes slot t, the same three slots for the whole CTA.  Row y of plane
+// z enters the ring as one coalesced line (cp.async, at least PF+1 steps
+// before its first reader), sites are updated in place, and a finished row
+// leaves as one coalesced line after its last reader.  In-place updating is
+// exact for the same reason as in the grid.  Neighbour rows, columns and
+// planes outside the tile belong to tiles one level below (W, S, B: swept)
+// or above (E, N, T: not yet swept): they are loaded like the tile's own
+// lines and never written back.
+#include <type_traits>
+
+#include "internal.h"
+#include "tiles.h"
+
+namespace stn {
+
+constexpr int kColPF = 2;  // steps of copies in flight ahead of their first reader
+// Ring depth: a cell's slot is refilled only after its row has been written
+// back: a row line lives from its copy (PF+1 steps before its first reader)
+// to its write-back (TX+2 steps after), so R >= TX + PF + 4, rounded up to a
+// multiple of 4.
+__host__ __device__ constexpr int col_ring_slots(int tx) { return (tx + kColPF + 4 + 3) / 4 * 4; }
+// Row pitch: TX + 2 cells, 12 for TX = 8 (a warp then spans four rows whose
+// cells fall on distinct 8-byte banks).
+__host__ __device__ constexpr int col_row_pitch(int tx) { return tx == 8 ? 12 : tx + 2; }
+template <typename T, int TX, int TY>
+constexpr size_t col_smem_bytes() {
+  return (size_t)col_ring_slots(TX) * (TY + 2) * col_row_pitch(TX) * sizeof(T);
+}
+
+template <typename T, class Ar, bool HAS_F, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) gs_column_kernel(T* u, const T* __restrict__ f, Geom g, Coef<T> c,
+                                                            const uint64_t* __restrict__ slices,
+                                                            const int* __restrict__ slice_off, TileGeom tg,
+                                                            int level) {
+  static_assert(TX >= 2 && TY >= 2, "tile of at least 2 x 2 columns");
+  constexpr int PF = kColPF;
+  constexpr int R = col_ring_slots(TX);
+  constexpr int RW = col_row_pitch(TX), RH = TY + 2;
+  constexpr int PL = RW * RH;  // cells per slot
+  constexpr int FQ = 4;        // right-hand side: register queue depth
+  extern __shared__ __align__(16) unsigned char gsc_raw[];
+  T* ring = reinterpret_cast<T*>(gsc_raw);
+  int I, J, K, p;
+  if (!find_task(tg, slices, slice_off, level, &I, &J, &K, &p)) return;
+  const int i = threadIdx.x, j = threadIdx.y;
+  const int x0 = I * TX, y0 = J * TY;
+  const int x = x0 + i, y = y0 + j;
+  const int z0 = K * tg.D;
+  const int nzl = min(g.nz - z0, tg.D);
+  const bool comp = x < g.nx && y < g.ny;
+  // copies (only elements of the padded grid): own row line (column i+1); the
+  // W / E column on the first / last lane (TX >= 2: never both); the S / N
+  // row on the first / last row (TY >= 2: never both)
+  const bool ldo = x <= g.nx && y <= g.ny;
+  const bool ldx = (i == 0 && y <= g.ny) || (i == TX - 1 && x0 + TX <= g.nx && y <= g.ny);
+  const bool ldy = (j == 0 && x <= g.nx) || (j == TY - 1 && y0 + TY <= g.ny && x <= g.nx);
+  const int64_t sy = g.sy;
+  // At step t: own-row and column copies of plane ql = t - j + 2 + PF into
+  // slot t + 2 + PF + i (column W: t + 1 + PF, column E: t + 2 + PF + TX);
+  // S row of plane t + 3 + PF and N row of plane t - TY + 2 + PF, both into
+  // slot t + 2 + PF + i; update of plane kk = t - i - j in slot t; write-back
+  // of plane qw = t - TX - j - 1 from slot t - TX - 1 + i.
+  const int ts = -3 - PF;            // first copies: plane -1 of row 0, plane 0 of the S row
+  const int te = nzl + TX + TY - 1;  // last write-back
+  // step windows (inclusive) of each duty
+  const int lo_l = j - 3 - PF, hi_l = j - 2 - PF + nzl;  // own row / columns, planes -1..nzl
+  const int lo_y = j == 0 ? -3 - PF : TY - 2 - PF;       // S / N row, planes 0..nzl-1
+  const int hi_y = lo_y + nzl - 1;
+  const int lo_c = i + j, hi_c = i + j + nzl - 1;        // update
+  const int lo_w = TX + j + 1, hi_w = TX + j + nzl;      // write-back, planes 0..nzl-1
+  auto inwin = [](int t, int lo, int hi) { return (unsigned)(t - lo) <= (unsigned)(hi - lo); };
+  auto mod = [](int q) { return ((q % R) + R) % R; };
+  // per-thread ring cells (slot 0) and the running slots of copies, update and write-back
+  T* const cell = ring + (j + 1) * RW + (i + 1);
+  T* const xcell = ring + (j + 1) * RW + (i == 0 ? 0 : TX + 1);
+  T* const ycell = ring + (j == 0 ? 0 : TY + 1) * RW + (i + 1);
+  const int xoff = i == 0 ? 1 + PF : 2 + PF + TX;  // column slot - t
+  int sl = mod(ts + 2 + PF + i), sx = mod(ts + xoff), sw = mod(ts - TX - 1 + i), st = mod(ts);
+  // global pointers at the plane of step ts
+  const T* go = u + (ldo ? g.at(x, y, z0) : 0) + (int64_t)(ts - j + 2 + PF) * sy;
+  const T* gx = u + (ldx ? g.at(i == 0 ? x0 - 1 : x0 + TX, y, z0) : 0) + (int64_t)(ts - j + 2 + PF) * sy;
+  const T* gy = u + (ldy ? g.at(x, j == 0 ? y0 - 1 : y0 + TY, z0) : 0) +
+                (int64_t)(j == 0 ? ts + 3 + PF : ts - TY + 2 + PF) * sy;
+  T* gw = u + (comp ? g.at(x, y, z0) : 0) + (int64_t)(ts - TX - j - 1) * sy;
+  // right-hand side of planes kk .. kk+FQ-1, kk = t - i - j
+  const T* gf = HAS_F ? f + (comp ? g.at(x, y, z0) : 0) + (int64_t)(ts - i - j + FQ) * sy : nullptr;
+  T F[FQ];
+#pragma unroll
+  for (int m = 0; m < FQ; ++m) {
+    const int q = ts - i - j + m;
+    F[m] = (HAS_F && comp && q >= 0 && q < nzl) ? f[g.at(x, y, z0 + q)] : T(0);
+  }
+  auto wrap = [](int s) { return s == R - 1 ? 0 : s + 1; };
+  for (int t = ts; t <= te; ++t) {
+    const bool wl = inwin(t, lo_l, hi_l);
+    if (ldo && wl) cp_async_elem(cell + sl * PL, go);
+    if (ldx && wl) cp_async_elem(xcell + sx * PL, gx);
+    if (ldy && inwin(t, lo_y, hi_y)) cp_async_elem(ycell + sl * PL, gy);
+    cp_async_commit();
+    if (comp && inwin(t, lo_c, hi_c)) {
+      const int sm1 = st == 0 ? R - 1 : st - 1, sp1 = wrap(st);
+      const T* pm = cell + sm1 * PL;
+      const T* pp = cell + sp1 * PL;
+      const T v = site_update<T, Ar, HAS_F, false>(pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], F[0], T(0), c);
+      cell[st * PL] = v;
+    }
+    if (comp && inwin(t, lo_w, hi_w)) *gw = cell[sw * PL];
+    if (HAS_F) {
+#pragma unroll
+      for (int m = 0; m + 1 < FQ; ++m) F[m] = F[m + 1];
+      const int q = t - i - j + FQ;
+      F[FQ - 1] = (comp && q >= 0 && q < nzl) ? *gf : T(0);
+      gf += sy;
+    }
+    cp_async_wait<PF>();
+    __syncthreads();
+    sl = wrap(sl); sx = wrap(sx); sw = wrap(sw); st = wrap(st);
+    go += sy; gx += sy; gy += sy; gw += sy;
+  }
+  cp_async_wait<0>();
+}
+
+template <typename T, class Ar, bool HAS_F, int TX, int TY>
+static int gs_column_levels(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tz, int nsweeps,
+                            cudaStream_t st) {
+  const TileGeom tg = make_tile_geom(g, TX, TY, tz, 1, nsweeps);
+  int rc = ensure_slices(ctx, tg, st);
+  if (rc) return rc;
+  const uint64_t* slices = slices_ptr(ctx);
+  const int* soff = slice_off_ptr(ctx);
+  auto kern = gs_column_kernel<T, Ar, HAS_F, TX, TY>;
+  const size_t smem = col_smem_bytes<T, TX, TY>();
+  cudaError_t e0 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e0 != cudaSuccess) return cuda_err(ctx, e0, "gs_column_kernel shared memory");
+  for (int L = 0; L < tg.nlevels; ++L) {
+    const int n = tasks_at_level(ctx, tg, L);
+    if (n == 0) continue;
+    kern<<<n, dim3(TX, TY), smem, st>>>(u, f, g, c, slices, soff, tg, L);
+    ctx->launches++;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "gs_column_kernel launch");
+  return STENCIL_OK;
+}
+
+// Column-march Gauss-Seidel: tiles tx x ty columns (8x8, 8x16, 16x8; default 8x8 for FP64, whose FP64
+// pipe favours the short ramp of narrow tiles, 16x8 for FP32) x tz planes (default:
+// equal chunks of at most 100 planes, enough tasks per level to fill the GPU while the march's ramp of
+// tx + ty steps stays short against the chunk).
+template <typename T, class Ar>
+int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,
+                  int nsweeps, cudaStream_t st) {
+  if (tx == 0) tx = sizeof(T) == 8 ? 8 : 16;
+  if (ty == 0) ty = 8;
+  if (tz <= 0) {
+    const int chunks = (g.nz + 99) / 100;
+    tz = (g.nz + chunks - 1) / chunks;
+  }
+#define GS_COL(TXX, TYY)                                                                     \
+  if (tx == TXX && ty == TYY)                                                                \
+    return f ? gs_column_levels<T, Ar, true, TXX, TYY>(ctx, u, f, g, c, tz, nsweeps, st)     \
+             : gs_column_levels<T, Ar, false, TXX, TYY>(ctx, u, f, g, c, tz, nsweeps, st);
+  GS_COL(8, 8)
+  GS_COL(8, 16)
+  GS_COL(16, 8)
+#undef GS_COL
+  return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column-march Gauss-Seidel tile %dx%d (supported 8x8, 8x16, 16x8)",
+                 tx, ty);
+}
+
+template int gs_column_run<double, ArithF64Fma>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>,
+                                                int, int, int, int, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x1Du>>(stencil_ctx*, double*, const double*, const Geom&,
+                                                       Coef<double>, int, int, int, int, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x15u>>(stencil_ctx*, double*, const double*, const Geom&,
+                                                       Coef<double>, int, int, int, int, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x12u>>(stencil_ctx*, double*, const double*, const Geom&,
+                                                       Coef<double>, int, int, int, int, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x10u>>(stencil_ctx*, double*, const double*, const Geom&,
+                                                       Coef<double>, int, int, int, int, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x00u>>(stencil_ctx*, double*, const double*, const Geom&,
+                                                       Coef<double>, int, int, int, int, cudaStream_t);
+template int gs_column_run<float, ArithF32>(stencil_ctx*, float*, const float*, const Geom&, Coef<float>, int, int,
+                                            int, int, cudaStream_t);
+
+}  // namespace stn

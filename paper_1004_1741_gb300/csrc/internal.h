@@ -76,6 +76,10 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
 template <typename T>
 int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
            const stencil_params* p, cudaStream_t st);
+// column-march Gauss-Seidel, one sweep per task (gs_column.cu); zero tile extents: defaults
+template <typename T, class Ar>
+int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,
+                  int nsweeps, cudaStream_t st);
 
 // Residual r = f - A u; optional FP64 r and/or FP32 r32 on the interior;
 // sums of r^2 and f^2 into the context's result slot (device) when
@@ -92,6 +96,7 @@ constexpr int STENCIL_UNSUPPORTED_TILE = 1;
 // Gauss-Seidel tasks 66 at 0, 71 at 1, 70.5 at 2
 constexpr int kDefaultIntAdds = 1;
 constexpr int kDefaultIntAddsJacobi = 2;
+constexpr int kDefaultIntAddsColumn = 2;
 void dataflow_release(stencil_ctx* ctx);  // internal: no kernel instantiated for a tile shape
 
 // Persistent dataflow run of the skewed-tile schedule over n grids (dataflow.cu).

@@ -87,19 +87,6 @@ __global__ void __launch_bounds__(32 * BY) jacobi_zmarch_kernel(const T* __restr
 // in flight.  Bandwidth-bound FP32 sweeps need that memory-level parallelism;
 // the FP64 sweep is FP64-pipe-bound either way.  One barrier per plane: the
 // buffer a new copy fills was last read two iterations earlier.
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-  if (sizeof(T) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 template <typename T, class Ar, bool HAS_F, bool WEIGHTED, int BY, int S>
 __global__ void __launch_bounds__(32 * BY) jacobi_pipe_kernel(const T* __restrict__ src, T* __restrict__ dst,
@@ -271,13 +258,16 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   if (!tmp) return status;
   const int nt = (p && p->nt > 0) ? p->nt : 1;
   const bool weighted0 = p && p->a != 0.0;
-  // FP32 with 2..4 sweeps per pass: on-chip temporal blocking is the default
-  const bool tbz_default = sizeof(T) == 4 && (!p || p->variant == 0) && nt >= 2 && nt <= 4 && !weighted0;
+  // FP32 with 1..4 sweeps per pass: the on-chip kernel is the default (two columns per thread and
+  // overlapped tiles beat the one-column z-march even at one sweep per pass); at one sweep per pass
+  // an explicit tile_y keeps the z-march it was chosen for
+  const bool tbz_default = sizeof(T) == 4 && (!p || p->variant == 0) && nt >= 1 && nt <= 4 && !weighted0 &&
+                           (nt > 1 || !p || p->tile_y == 0);
   if (tbz_default) {
     cudaError_t e0 = cudaMemcpyAsync(tmp, u, bytes, cudaMemcpyDeviceToDevice, st);
     if (e0 != cudaSuccess) return cuda_err(ctx, e0, "cudaMemcpyAsync(jacobi halo)");
     stencil_params q = p ? *p : stencil_params{};
-    if (!q.tile_y) q.tile_y = 16;
+    if (!q.tile_y) q.tile_y = nt == 1 ? 16 : 32;
     if (!q.tile_z) q.tile_z = 64;
     return tbz_run<T>(ctx, u, tmp, f, g, h, nsweeps, nt, &q, st);
   }

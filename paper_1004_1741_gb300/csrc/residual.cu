@@ -219,20 +219,18 @@ int stencil_solve_mixed(stencil_ctx* ctx, double* u, const double* f, const int6
     e = cudaMemsetAsync(e32, 0, n * sizeof(float), st);
     if (e != cudaSuccess) return cuda_err(ctx, e, "memset e32");
     // FP32 inner sweeps: Jacobi with on-chip temporal blocking (3 sweeps per
-    // pass), Gauss-Seidel with 4 sweeps per task on 32x8x8 skewed tiles
+    // pass), Gauss-Seidel as the column march (one sweep per task)
     stencil_params q{};
     q.int_adds = -1;
     if (smoother == STENCIL_JACOBI) {
       q.variant = 4;
       q.nt = 3;
-      q.tile_y = 16;
+      q.tile_y = 32;
       q.tile_z = 64;
       rc = jacobi_run<float>(ctx, e32, r32, g, h, inner_sweeps, &q, st);
     } else {
-      q.nt = inner_sweeps >= 4 ? 4 : 1;
-      q.tile_x = 32;
-      q.tile_y = 8;
-      q.tile_z = 8;
+      q.nt = 1;
+      q.variant = 4;
       rc = gs_run<float>(ctx, e32, r32, g, h, inner_sweeps, &q, st);
     }
     if (rc) return rc;

@@ -15,6 +15,8 @@
 // costs ALU work, which FP32 has plenty of, and buys a single read and a
 // single write of the grid per NT sweeps.  (The FP64 pipe has no such slack:
 // FP64 uses the no-recomputation skewed-tile schedule instead.)
+#include <type_traits>
+
 #include "internal.h"
 
 namespace stn {
@@ -67,15 +69,26 @@ __global__ void __launch_bounds__(32 * BY) jacobi_tbz_kernel(const T* __restrict
 #pragma unroll
     for (int i = 0; i < PF; ++i)
       qv[k][i] = (valid[k] && zs + i <= ze) ? src[col[k] + (int64_t)(zs + i + 1) * sy] : T(0);
-  for (int q = zs; q <= z1 - 1 + NT; ++q) {
-    const int b = q & 1, bp = b ^ 1;
+  // per-column pointers at the plane each one serves after step q = zs; advanced by one plane per step
+  // and dereferenced only when that plane exists
+  const T* pq[2];   // level-0 load: plane q + PF
+  const T* pfq[2];  // right-hand side at plane q (level l reads plane q - l)
+  T* pd[2];         // output: plane q - NT
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    pq[k] = src + col[k] + (int64_t)(zs + PF + 1) * sy;
+    pfq[k] = HAS_F ? f + col[k] + (int64_t)(zs + 1) * sy : nullptr;
+    pd[k] = dst + col[k] + (int64_t)(zs - NT + 1) * sy;
+  }
+  auto step = [&](int q, auto bc) {
+    constexpr int b = decltype(bc)::value, bp = b ^ 1;
     // level 0: plane q
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const T v = qv[k][0];
 #pragma unroll
       for (int i = 0; i + 1 < PF; ++i) qv[k][i] = qv[k][i + 1];
-      qv[k][PF - 1] = (valid[k] && q + PF <= ze) ? src[col[k] + (int64_t)(q + PF + 1) * sy] : T(0);
+      qv[k][PF - 1] = (valid[k] && q + PF <= ze) ? *pq[k] : T(0);
       P[k][0] = C[k][0];
       C[k][0] = N[k][0];
       N[k][0] = v;
@@ -91,7 +104,7 @@ __global__ void __launch_bounds__(32 * BY) jacobi_tbz_kernel(const T* __restrict
         T v;
         if (interior[k] && p >= 0 && p < g.nz) {
           T fv = T(0);
-          if (HAS_F) fv = f[col[k] + (int64_t)(p + 1) * sy];
+          if (HAS_F) fv = pfq[k][-(int64_t)l * sy];
           v = site_update<T, Ar, HAS_F, false>(SM(l - 1, bp, ty, xm[k]), SM(l - 1, bp, ty, xp[k]),
                                                SM(l - 1, bp, ym, tc), SM(l - 1, bp, yp, tc), P[k][l - 1],
                                                N[k][l - 1], fv, T(0), c);
@@ -104,12 +117,27 @@ __global__ void __launch_bounds__(32 * BY) jacobi_tbz_kernel(const T* __restrict
           N[k][l] = v;
           SM(l, b, ty, tc) = v;
         } else if (out[k] && p >= z0 && p < z1) {
-          dst[col[k] + (int64_t)(p + 1) * sy] = v;
+          *pd[k] = v;
         }
       }
     }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      pq[k] += sy;
+      if (HAS_F) pfq[k] += sy;
+      pd[k] += sy;
+    }
     __syncthreads();
+  };
+  // the buffer index of step q is q & 1; two steps per trip keep it a constant
+  const int qe = z1 - 1 + NT;
+  int q = zs;
+  if (q & 1) step(q++, std::integral_constant<int, 1>{});
+  for (; q + 1 <= qe; q += 2) {
+    step(q, std::integral_constant<int, 0>{});
+    step(q + 1, std::integral_constant<int, 1>{});
   }
+  if (q <= qe) step(q, std::integral_constant<int, 0>{});
 #undef SM
 }
 

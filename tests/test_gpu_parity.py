@@ -160,6 +160,45 @@ def test_gs_f64_tiles_temporal(ctx, tile, nt, variant):
                   oracle.gs_lex(u0, f0, 0.07, ns), "gs %s nt=%d variant %d" % (tile, nt, variant))
 
 
+@pytest.mark.parametrize("dims", RAGGED + [(45, 38, 29), (70, 9, 33), (20, 20, 2), (17, 18, 3)])
+@pytest.mark.parametrize("tile", [(0, 0, 0), (16, 8, 0), (8, 16, 0), (16, 8, 7), (8, 8, 13), (8, 16, 40), (8, 8, 1),
+                                  (16, 8, 2), (8, 8, 1000)])
+@pytest.mark.parametrize("variant", [4])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_gs_column_march(ctx, dims, tile, variant, dtype):
+    """variant 4: one thread per column marching up the tile-local wavefront, chunked or whole
+    columns (odd chunks, chunks of one plane), ragged tiles, odd and even sweep counts, with and
+    without f."""
+    u0, f0 = W.random_grid(*dims, seed=11, dtype=dtype, with_f=True)
+    for ns, ff in ((1, f0), (4, None), (7, f0)):
+        _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, ff, 0.04, ns, tile=tile, variant=variant),
+                      oracle.gs_lex(u0, ff, 0.04, ns), "gs column v%d %s %s ns=%d" % (variant, dims, tile, ns))
+
+
+@pytest.mark.parametrize("int_adds", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [4])
+def test_gs_column_int_adds(ctx, int_adds, variant):
+    """Every integer-pipe share of the column march gives the oracle's bits (Laplace field, where
+    the integer path is taken, and a random field with f)."""
+    u0 = W.laplace_cube(70, 1, 2)
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, None, 1.0, 9, variant=variant, int_adds=int_adds),
+                  oracle.gs_lex(u0, None, 1.0, 9), "gs column laplace int_adds=%d" % int_adds)
+    u1, f1 = W.random_grid(41, 35, 30, seed=int_adds, with_f=True)
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u1, f1, 0.2, 5, variant=variant, int_adds=int_adds,
+                       tile=(16, 8, 9)),
+                  oracle.gs_lex(u1, f1, 0.2, 5), "gs column random int_adds=%d" % int_adds)
+
+
+def test_gs_column_rejects_nt(ctx):
+    u = _dev(W.random_grid(9, 9, 9, seed=1)[0])
+    with pytest.raises(capi.StencilError):
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, nt=2, variant=4)
+    with pytest.raises(capi.StencilError):
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, tile=(32, 16, 0), variant=4)
+    with pytest.raises(capi.StencilError):
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, variant=5)
+
+
 @pytest.mark.parametrize("nt", [1, 4, 8])
 @pytest.mark.parametrize("variant", [1, 2])
 def test_gs_f32_temporal(ctx, nt, variant):
@@ -358,6 +397,6 @@ def test_full_size_400_bench_config(ctx, smoother):
     with cf.ThreadPoolExecutor(1) as ex:  # the oracle releases the GIL inside C
         fut = ex.submit(oracle.jacobi if smoother == "jacobi" else oracle.gs_lex, u0, None, 1.0, 100)
         fn = capi.stencil_jacobi if smoother == "jacobi" else capi.stencil_gs_lex
-        got = _run(ctx, fn, u0, None, 1.0, 100, nt=cfg["nt"], tile=cfg["tile"])
+        got = _run(ctx, fn, u0, None, 1.0, 100, nt=cfg["nt"], tile=cfg["tile"], variant=cfg["variant"])
         ref = fut.result()
     _assert_exact(got, ref, "400^3 %s" % smoother)
