@@ -53,34 +53,38 @@ struct ArithF32 {
 // The FP64 pipe of a GB300 SM retires ~1.6 lanes per clock, while its
 // integer pipes issue far more, so an FP64-bound kernel leaves most issue
 // slots idle.  int_add_f64 computes the IEEE-754 round-to-nearest-even sum of
-// two doubles with 64-bit integer arithmetic when both are non-negative, the
-// larger is normal and below 2^1022, and the smaller is +0 or normal at most
+// two doubles with 32-bit integer arithmetic when both are positive and
+// normal, the larger has exponent field 11..2045 and the smaller lies at most
 // 10 binades below it (the common case for neighbouring values of a smoothed
-// field); otherwise it reports failure and the caller uses the FP64 pipe.
-// Method: the significands (implicit bit at bit 62) are aligned within ten
-// guard bits, so no bit is shifted out and no sticky bit is needed; the sum is
-// rounded to 53 bits, to nearest with ties to even, by adding
-// 2^(k-1) - 1 + (bit k of the sum) before the shift by k = 10 or 11 (one more
-// when the addition carried into bit 63); a carry out of the rounding ripples
-// into the exponent field.
+// field; the exponent bound makes the smaller operand normal whenever the gap
+// is at most 10); otherwise it reports failure and the caller uses the FP64
+// pipe.  Method: with ten guard bits the larger significand (implicit bit at
+// 62) and the smaller one, shifted by 10 - gap, add exactly in 64 bits.  A
+// carry into bit 63 is folded back by one right shift that ORs the dropped
+// bit into bit 0 (it only matters as a sticky bit), so the sum always rounds
+// at bit 10: to nearest with ties to even, by adding 2^9 - 1 + (bit 10)
+// before the shift; a carry out of the rounding ripples into the exponent.
 __device__ __forceinline__ bool int_add_f64(double a, double b, double* out) {
-  const unsigned long long A = (unsigned long long)__double_as_longlong(a);
-  const unsigned long long B = (unsigned long long)__double_as_longlong(b);
-  const unsigned ea = (unsigned)(A >> 52), eb = (unsigned)(B >> 52);  // sign bit included: negatives fail below
-  const bool sw = eb > ea;
-  const unsigned long long H = sw ? B : A, L = sw ? A : B;
-  const unsigned eh = sw ? eb : ea, el = sw ? ea : eb;
-  const unsigned d = eh - el;
-  const bool lzero = L == 0ull;
-  if (!((eh - 1u) < 2045u && (lzero || (el >= 1u && d <= 10u)))) return false;
-  const unsigned long long FRAC = 0xFFFFFFFFFFFFFull, ONE = 1ull << 52;
-  const unsigned long long MH = ((H & FRAC) | ONE) << 10;
-  const unsigned long long ML = lzero ? 0ull : ((((L & FRAC) | ONE) << 10) >> d);
+  const unsigned ahi = (unsigned)__double2hiint(a), alo = (unsigned)__double2loint(a);
+  const unsigned bhi = (unsigned)__double2hiint(b), blo = (unsigned)__double2loint(b);
+  const bool sw = (bhi >> 20) > (ahi >> 20);  // sign bit included: negatives fail below
+  const unsigned hhi = sw ? bhi : ahi, hlo = sw ? blo : alo;
+  const unsigned lhi = sw ? ahi : bhi, llo = sw ? alo : blo;
+  const unsigned eh = hhi >> 20;
+  const unsigned d = eh - (lhi >> 20);
+  if (!((eh - 11u) < 2035u && d <= 10u)) return false;
+  const unsigned mh = (hhi & 0xFFFFFu) | 0x100000u, ml = (lhi & 0xFFFFFu) | 0x100000u;
+  const unsigned sh = 10u - d;
+  const unsigned long long MH = ((unsigned long long)__funnelshift_l(hlo, mh, 10) << 32) | (hlo << 10);
+  const unsigned long long ML = ((unsigned long long)__funnelshift_l(llo, ml, sh) << 32) | (llo << sh);
   const unsigned long long S = MH + ML;  // < 2^64
-  const unsigned c = (unsigned)(S >> 63);
-  const unsigned k = 10u + c;
-  const unsigned long long M = (S + ((1ull << (k - 1u)) - 1ull + ((S >> k) & 1ull))) >> k;
-  *out = __longlong_as_double((long long)(((unsigned long long)(eh + c - 1u) << 52) + M));
+  const unsigned shi = (unsigned)(S >> 32), slo = (unsigned)S;
+  const unsigned c = shi >> 31;
+  const unsigned s2lo = __funnelshift_r(slo, shi, c) | (slo & c), s2hi = shi >> c;
+  const unsigned long long R = (((unsigned long long)s2hi << 32) | s2lo) + (0x1FFu + ((s2lo >> 10) & 1u));
+  const unsigned rlo = (unsigned)R, rhi = (unsigned)(R >> 32);
+  const unsigned mlo = __funnelshift_r(rlo, rhi, 10), mhi = (rhi >> 10) + ((eh + c - 1u) << 20);
+  *out = __hiloint2double((int)mhi, (int)mlo);
   return true;
 }
 

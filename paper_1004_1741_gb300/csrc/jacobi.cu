@@ -291,7 +291,7 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   if (int_adds < 0 || int_adds > 5)
     return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
   Coef<T> c = make_coef<T>(h, p);
-  int by = (p && p->tile_y) ? p->tile_y : 8;
+  int by = (p && p->tile_y) ? p->tile_y : (sizeof(T) == 8 ? 4 : 8);  // FP64: 32x4 measured fastest
   if (by != 4 && by != 8 && by != 16)
     return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Jacobi tile_y = %d (supported 4, 8, 16)", by);
   if (p && p->tile_x && p->tile_x != 32)

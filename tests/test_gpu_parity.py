@@ -234,7 +234,7 @@ def test_int_adds_bit_exact(ctx, int_adds, smoother, dims):
         u0, f0 = W.random_grid(*dims, seed=int_adds, with_f=poisson)
         _assert_exact(_run(ctx, fn, u0, f0, 0.1, 5, int_adds=int_adds), ofn(u0, f0, 0.1, 5),
                       "%s int_adds=%d poisson=%s" % (smoother, int_adds, poisson))
-    z0 = np.zeros((dims[2] + 2, dims[1] + 2, dims[0] + 2))  # zeros everywhere: the +0 operand case
+    z0 = np.zeros((dims[2] + 2, dims[1] + 2, dims[0] + 2))  # zeros everywhere: +0 operands take the FP64 pipe
     z0[0] = 0.75
     _assert_exact(_run(ctx, fn, z0, None, 1.0, 4, int_adds=int_adds), ofn(z0, None, 1.0, 4), "zeros")
 
