@@ -31,7 +31,7 @@ SWEEPS = 100
 # the launch configuration timed for the headline (tests/test_gpu_parity.py checks it at full size)
 HEADLINE = {
     "jacobi": {"nt": 1, "tile": (32, 4, 0), "variant": 0},
-    "gs": {"nt": 1, "tile": (8, 8, 0), "variant": 4},
+    "gs": {"nt": 1, "tile": (8, 8, 0), "variant": 5},
 }
 NT_SWEEP = [1, 2, 4, 8, 16]
 METRIC = "GLUP/s at 400^3 FP64 (Jacobi, GS) vs HBM roofline; batched/served vs plain, p99"
@@ -277,7 +277,8 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (the smoother call that took longer)
     dom = "gs" if acc["g"] >= acc["j"] else "jacobi"
-    kern = "gs_column_kernel" if dom == "gs" else "jacobi_zmarch_kernel"
+    kern = ({4: "gs_column_kernel", 5: "dataflow_column_kernel"}.get(cg["variant"], "gs_direct_kernel")
+            if dom == "gs" else "jacobi_zmarch_kernel")
     nlaunch = (args.steps and (launch_counts(ctx, dom, cj if dom == "jacobi" else cg))) or 1
     dur_s = (acc["g"] if dom == "gs" else acc["j"]) / 1e3 / (args.steps * nlaunch)
     flops_per_launch = FP64_OPS_PER_LUP * SWEEPS * N ** 3 / nlaunch

@@ -108,6 +108,8 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          tile_x x tile_y columns (8x8, 8x16, 16x8) x tile_z planes, one
  *          thread per column marching up the tile-local wavefront through a
  *          shared-memory ring (one launch per task level);
+ *          5 = the column march as one persistent dataflow launch over the
+ *          tasks (blocking, like 3; no launch boundary between levels);
  *          Gauss-Seidel default: variant 4 at nt = 1 without a tile (8x8
  *          for FP64, 16x8 for FP32, chunks of at most 100 planes),
  *          variant 2 otherwise;
@@ -182,15 +184,17 @@ int residual_norm(stencil_ctx* ctx, const double* u, const double* f, const int6
                   double* r_out, double* out_abs, double* out_rel, void* stream);
 
 /* Batched smoothing of n independent grids of uneven sizes in ONE persistent
- * kernel launch, replayed from a CUDA graph (not in the paper; the tile tasks
- * of all grids share one dependency-ordered work queue, so small grids fill
- * the GPU together).  u[i], f[i]: device pointers of grid i (f may be NULL,
+ * kernel launch, replayed from a CUDA graph (not in the paper; the tasks of
+ * all grids share one dependency-ordered work queue, so small grids fill the
+ * GPU together).  u[i], f[i]: device pointers of grid i (f may be NULL,
  * or f[i] NULL, for f = 0); dims[3i..3i+2] its interior extents; h[i],
  * nsweeps[i] (host arrays).  smoother: STENCIL_JACOBI or STENCIL_GS; dtype:
  * STENCIL_F64 or STENCIL_F32 (u and f are double* or float* accordingly).
  * Every grid ends exactly as after stencil_jacobi / stencil_gs_lex with the
- * same arguments.  params (may be NULL): nt and tile shared by all grids
- * (defaults: GS 16^3, Jacobi 32x8x8, nt = 1); a must be 0.  Jacobi takes a
+ * same arguments.  params (may be NULL): nt, tile, b and int_adds shared by
+ * all grids (defaults nt = 1; Gauss-Seidel at nt = 1: column-march tasks of
+ * 8x8 columns (16x8 for FP32) x 100 planes unless variant is 1..3, else
+ * 16^3 tile tasks; Jacobi 32x8x8 tile tasks); a must be 0.  Jacobi takes a
  * workspace of the total size of the batch.  Blocking: returns when the batch
  * is done; STENCIL_ERR_TIMEOUT if a bounded device wait expired (the grids
  * are then undefined, the context stays usable). */

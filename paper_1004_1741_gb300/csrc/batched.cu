@@ -22,6 +22,25 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
     total += (size_t)geoms[(size_t)i].sy * (size_t)(geoms[(size_t)i].nz + 2);
   }
   const int nt = (p && p->nt > 0) ? p->nt : 1;
+  // Gauss-Seidel with one sweep per pass runs the column-march tasks unless a tile-task variant is asked for
+  const bool column = smoother == STENCIL_GS && nt == 1 && (!p || p->variant == 0 || p->variant >= 4);
+  if (column) {
+    if (p && p->a != 0.0) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "weighted sweeps are not batched");
+    const int cx = (p && p->tile_x) ? p->tile_x : (sizeof(T) == 8 ? 8 : 16);
+    const int cy = (p && p->tile_y) ? p->tile_y : 8;
+    const int cz = (p && p->tile_z) ? p->tile_z : 100;
+    const int ia = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsColumn;
+    if (ia > 5) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", ia);
+    std::vector<T*> a((size_t)n);
+    std::vector<const T*> fs((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      a[(size_t)i] = (T*)u[i];
+      fs[(size_t)i] = f ? (const T*)f[i] : nullptr;
+    }
+    const double bco = (p && p->b != 0.0) ? p->b : 1.0 / 6.0;
+    return dataflow_run<T>(ctx, DF_KIND_GS_COLUMN, n, a.data(), nullptr, fs.data(), geoms.data(), nsweeps, h, cx, cy,
+                           cz, 1, ctx->df_timeout_ns, ctx->df_poison, st, (double)(T)bco, ia);
+  }
   const int W = (p && p->tile_x) ? p->tile_x : (smoother == STENCIL_GS ? 16 : 32);
   const int H = (p && p->tile_y) ? p->tile_y : (smoother == STENCIL_GS ? 16 : 8);
   const int D = (p && p->tile_z) ? p->tile_z : (smoother == STENCIL_GS ? 16 : 8);
@@ -51,8 +70,9 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
       b[(size_t)i] = odd ? (T*)u[i] : ti;
     }
   }
+  const double bco = (p && p->b != 0.0) ? p->b : 1.0 / 6.0;
   return dataflow_run<T>(ctx, smoother, n, a.data(), smoother == STENCIL_JACOBI ? b.data() : nullptr, fs.data(),
-                         geoms.data(), nsweeps, h, W, H, D, nt, ctx->df_timeout_ns, ctx->df_poison, st);
+                         geoms.data(), nsweeps, h, W, H, D, nt, ctx->df_timeout_ns, ctx->df_poison, st, (double)(T)bco);
 }
 
 }  // namespace stn

@@ -22,90 +22,12 @@
 #include <numeric>
 #include <vector>
 
+#include "dataflow.cuh"
 #include "internal.h"
 #include "task_bodies.cuh"
 #include "tiles.h"
 
 namespace stn {
-
-struct DFGridDesc {
-  void* a;        // Gauss-Seidel: the grid; Jacobi: grid of even levels
-  void* b;        // Jacobi: grid of odd levels
-  const void* f;  // right-hand side or nullptr
-  Geom g;
-  TileGeom tg;
-  double bco, hh;
-  long long flag_base;
-};
-
-struct DFRun {
-  const DFGridDesc* grids;
-  const int4* tasks;  // x = grid, y = I, z = J | K << 16, w = p
-  long long ntasks;
-  unsigned int* flags;
-  unsigned long long* counter;
-  int* error;  // [0] status (0 or STENCIL_ERR_TIMEOUT), [1] queue index that gave up
-  long long timeout_ns;
-  long long poison;  // queue index whose completion is never published (failure tests), -1 = none
-};
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ long long global_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ long long df_flag(const DFGridDesc& d, int I, int J, int K, int p) {
-  const TileGeom& t = d.tg;
-  return d.flag_base + (((long long)p * t.NK + K) * t.NJ + J) * t.NI + I;
-}
-
-// Thread 0: wait until every dependency of the task is published; false on timeout/error.
-__device__ bool df_wait(const DFRun& run, const DFGridDesc& d, int I, int J, int K, int p, long long qi) {
-  long long deps[11];
-  int n = 0;
-  if (I > 0) deps[n++] = df_flag(d, I - 1, J, K, p);
-  if (J > 0) deps[n++] = df_flag(d, I, J - 1, K, p);
-  if (K > 0) deps[n++] = df_flag(d, I, J, K - 1, p);
-  if (p > 0) {
-    const TileGeom& t = d.tg;
-    if (t.nt == 1) {
-      deps[n++] = df_flag(d, I, J, K, p - 1);
-      if (I + 1 < t.NI) deps[n++] = df_flag(d, I + 1, J, K, p - 1);
-      if (J + 1 < t.NJ) deps[n++] = df_flag(d, I, J + 1, K, p - 1);
-      if (K + 1 < t.NK) deps[n++] = df_flag(d, I, J, K + 1, p - 1);
-    } else {
-      for (int c = 0; c < 2; ++c)
-        for (int b = 0; b < 2; ++b)
-          for (int a = 0; a < 2; ++a)
-            if (I + a < t.NI && J + b < t.NJ && K + c < t.NK) deps[n++] = df_flag(d, I + a, J + b, K + c, p - 1);
-    }
-  }
-  const long long t0 = global_ns();
-  for (int i = 0; i < n; ++i) {
-    const unsigned* fl = run.flags + deps[i];
-    unsigned spins = 0;
-    while (ld_acquire(fl) == 0u) {
-      if ((++spins & 63u) == 0u) {
-        if (*(volatile int*)run.error != 0) return false;
-        if (global_ns() - t0 > run.timeout_ns) {
-          if (atomicCAS(run.error, 0, STENCIL_ERR_TIMEOUT) == 0) run.error[1] = (int)qi;
-          return false;
-        }
-      }
-      __nanosleep(64);
-    }
-  }
-  return true;
-}
 
 template <typename T, int KIND, int W, int H, int D>
 __global__ void __launch_bounds__(GS_THREADS) dataflow_kernel(DFRun run, SiteTable tb) {
@@ -277,13 +199,16 @@ static int plan_build(stencil_ctx* ctx, DFPlan* pl, int kind, int n, const Geom*
 }
 
 template <typename T>
-static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, int D, const SiteTable& tb) {
+static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, int D, const SiteTable& tb,
+                        int int_adds) {
   cudaStream_t gs = ctx->gstream;
   cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamBeginCapture");
   int rc = STENCIL_OK;
   e = cudaMemsetAsync(pl->dev + pl->b_desc + pl->b_task, 0, pl->b_flag + 256, gs);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && kind == DF_KIND_GS_COLUMN) {
+    rc = df_column_launch<T>(ctx, pl->run, W, H, int_adds, gs);
+  } else if (e == cudaSuccess) {
     rc = STENCIL_UNSUPPORTED_TILE;
 #define DF_TILE(WW, HH, DD)                                                                          \
   if (W == WW && H == HH && D == DD)                                                                 \
@@ -321,7 +246,7 @@ static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, in
 template <typename T>
 int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, const T* const* f, const Geom* geoms,
                  const int* nsweeps, const double* h, int W, int H, int D, int nt, long long timeout_ns,
-                 long long poison, cudaStream_t st) {
+                 long long poison, cudaStream_t st, double bco, int int_adds) {
   cudaError_t e;
   if (!ctx->gstream) {
     e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
@@ -336,7 +261,7 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
     if (e != cudaSuccess) return cuda_err(ctx, e, "cudaMallocHost(status word)");
   }
   // ---- find or build the plan of this shape
-  std::vector<long long> key = {(long long)sizeof(T), kind, n, W, H, D, nt};
+  std::vector<long long> key = {(long long)sizeof(T), kind, n, W, H, D, nt, int_adds};
   for (int i = 0; i < n; ++i) {
     key.push_back(geoms[i].nx);
     key.push_back(geoms[i].ny);
@@ -377,7 +302,7 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
   if (!pl->exec || pl->exec_timeout != timeout_ns || pl->exec_poison != poison || pl->exec_tb != tb.coords) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     pl->exec = nullptr;
-    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, tb);
+    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, tb, int_adds);
     if (rc) return rc;
     pl->exec_timeout = timeout_ns;
     pl->exec_poison = poison;
@@ -394,7 +319,7 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
     d.g = geoms[i];
     d.tg = make_tile_geom(geoms[i], W, H, D, nt, nsweeps[i]);
     if (nsweeps[i] == 0 || geoms[i].nx == 0 || geoms[i].ny == 0 || geoms[i].nz == 0) d.tg.npass = 0;
-    d.bco = 1.0 / 6.0;
+    d.bco = bco;
     d.hh = h[i] * h[i];
     d.flag_base = fbase;
     fbase += (long long)d.tg.NI * d.tg.NJ * d.tg.NK * d.tg.npass;
@@ -418,9 +343,9 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
 
 template int dataflow_run<double>(stencil_ctx*, int, int, double* const*, double* const*, const double* const*,
                                   const Geom*, const int*, const double*, int, int, int, int, long long, long long,
-                                  cudaStream_t);
+                                  cudaStream_t, double, int);
 template int dataflow_run<float>(stencil_ctx*, int, int, float* const*, float* const*, const float* const*,
                                  const Geom*, const int*, const double*, int, int, int, int, long long, long long,
-                                 cudaStream_t);
+                                 cudaStream_t, double, int);
 
 }  // namespace stn

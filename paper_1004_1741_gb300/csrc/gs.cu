@@ -333,17 +333,18 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
   c.b = (T)((p && p->b != 0.0) ? p->b : 1.0 / 6.0);
   c.hh = (T)(h * h);
   const int tx = p ? p->tile_x : 0, ty = p ? p->tile_y : 0, tz = p ? p->tile_z : 0;
+  const bool persistent = p && p->variant == 5;
   const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsColumn;
   if (int_adds < 0 || int_adds > 5)
     return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
   if constexpr (sizeof(T) == 8) {
-    if (int_adds == 1) return gs_column_run<T, ArithF64Mix<0x1Du>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, st);
-    if (int_adds == 2) return gs_column_run<T, ArithF64Mix<0x15u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, st);
-    if (int_adds == 3) return gs_column_run<T, ArithF64Mix<0x12u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, st);
-    if (int_adds == 4) return gs_column_run<T, ArithF64Mix<0x10u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, st);
-    if (int_adds == 5) return gs_column_run<T, ArithF64Mix<0x00u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, st);
+    if (int_adds == 1) return gs_column_run<T, ArithF64Mix<0x1Du>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+    if (int_adds == 2) return gs_column_run<T, ArithF64Mix<0x15u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+    if (int_adds == 3) return gs_column_run<T, ArithF64Mix<0x12u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+    if (int_adds == 4) return gs_column_run<T, ArithF64Mix<0x10u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+    if (int_adds == 5) return gs_column_run<T, ArithF64Mix<0x00u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
   }
-  return gs_column_run<T, typename DefaultArith<T>::type>(ctx, u, f, g, c, tx, ty, tz, nsweeps, st);
+  return gs_column_run<T, typename DefaultArith<T>::type>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
 }
 
 template <typename T>
@@ -351,12 +352,13 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
            cudaStream_t st) {
   if (nsweeps == 0 || g.nx == 0 || g.ny == 0 || g.nz == 0) return STENCIL_OK;
   const int nt = (p && p->nt > 0) ? p->nt : 1;
-  // variant: in place through L1 or the staged shared-memory box; 4: column march
+  // variant: in place through L1 or the staged shared-memory box; 4: column march, one launch per
+  // level; 5: column march, one persistent dataflow launch
   const int variant = p ? p->variant : 0;
-  if (variant < 0 || variant > 4) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
+  if (variant < 0 || variant > 5) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
   // one sweep per pass without an explicit tile: the column march is the default
   const bool tiled = p && (p->tile_x || p->tile_y || p->tile_z);
-  if (variant == 4 || (variant == 0 && nt == 1 && !tiled)) {
+  if (variant == 4 || variant == 5 || (variant == 0 && nt == 1 && !tiled)) {
     if (nt != 1) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column-march Gauss-Seidel runs nt = 1 only");
     return gs_column_dispatch<T>(ctx, u, f, g, h, nsweeps, p, st);
   }

@@ -24,6 +24,7 @@
 // lines and never written back.
 #include <type_traits>
 
+#include "dataflow.cuh"
 #include "internal.h"
 #include "tiles.h"
 
@@ -43,21 +44,18 @@ constexpr size_t col_smem_bytes() {
   return (size_t)col_ring_slots(TX) * (TY + 2) * col_row_pitch(TX) * sizeof(T);
 }
 
+// The task (I, J, K, p): sweep p of tile (I, J, K) in place on u; all threads
+// of the CTA (TX x TY) take part; ring: col_smem_bytes of shared memory.
+// Returns after a barrier, with all of the task's global writes issued.
 template <typename T, class Ar, bool HAS_F, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) gs_column_kernel(T* u, const T* __restrict__ f, Geom g, Coef<T> c,
-                                                            const uint64_t* __restrict__ slices,
-                                                            const int* __restrict__ slice_off, TileGeom tg,
-                                                            int level) {
+__device__ __forceinline__ void gs_column_body(T* u, const T* __restrict__ f, const Geom& g, const Coef<T>& c,
+                                               const TileGeom& tg, int I, int J, int K, T* ring) {
   static_assert(TX >= 2 && TY >= 2, "tile of at least 2 x 2 columns");
   constexpr int PF = kColPF;
   constexpr int R = col_ring_slots(TX);
   constexpr int RW = col_row_pitch(TX), RH = TY + 2;
   constexpr int PL = RW * RH;  // cells per slot
   constexpr int FQ = 4;        // right-hand side: register queue depth
-  extern __shared__ __align__(16) unsigned char gsc_raw[];
-  T* ring = reinterpret_cast<T*>(gsc_raw);
-  int I, J, K, p;
-  if (!find_task(tg, slices, slice_off, level, &I, &J, &K, &p)) return;
   const int i = threadIdx.x, j = threadIdx.y;
   const int x0 = I * TX, y0 = J * TY;
   const int x = x0 + i, y = y0 + j;
@@ -134,6 +132,64 @@ __global__ void __launch_bounds__(TX * TY) gs_column_kernel(T* u, const T* __res
     go += sy; gx += sy; gy += sy; gw += sy;
   }
   cp_async_wait<0>();
+  __syncthreads();
+}
+
+// One launch per task level (find_task: CTA -> task of the level).
+template <typename T, class Ar, bool HAS_F, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) gs_column_kernel(T* u, const T* __restrict__ f, Geom g, Coef<T> c,
+                                                            const uint64_t* __restrict__ slices,
+                                                            const int* __restrict__ slice_off, TileGeom tg,
+                                                            int level) {
+  extern __shared__ __align__(16) unsigned char gsc_raw[];
+  int I, J, K, p;
+  if (!find_task(tg, slices, slice_off, level, &I, &J, &K, &p)) return;
+  gs_column_body<T, Ar, HAS_F, TX, TY>(u, f, g, c, tg, I, J, K, reinterpret_cast<T*>(gsc_raw));
+}
+
+// Persistent form: each CTA takes the next task of the level-ordered queue,
+// waits (bounded) for the tasks it depends on, runs the column march and
+// publishes its completion (dataflow.cuh).  No launch boundaries, no idle tail
+// per level.
+template <typename T, class Ar, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) dataflow_column_kernel(DFRun run) {
+  extern __shared__ __align__(16) unsigned char gsc_raw[];
+  T* ring = reinterpret_cast<T*>(gsc_raw);
+  __shared__ long long s_q;
+  const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+  for (;;) {
+    if (lead) {
+      long long q = -1;
+      if (*(volatile int*)run.error == 0) {
+        const unsigned long long got = atomicAdd(run.counter, 1ULL);
+        if ((long long)got < run.ntasks) q = (long long)got;
+      }
+      if (q >= 0) {
+        const int4 tk = run.tasks[q];
+        if (!df_wait(run, run.grids[tk.x], tk.y, tk.z & 0xFFFF, tk.z >> 16, tk.w, q)) q = -1;
+      }
+      s_q = q;
+    }
+    __syncthreads();
+    const long long q = s_q;
+    if (q < 0) return;
+    const int4 tk = run.tasks[q];
+    const DFGridDesc& d = run.grids[tk.x];
+    const int I = tk.y, J = tk.z & 0xFFFF, K = tk.z >> 16, p = tk.w;
+    Coef<T> c;
+    c.a = T(0);
+    c.b = (T)d.bco;
+    c.hh = (T)d.hh;
+    if (d.f)
+      gs_column_body<T, Ar, true, TX, TY>((T*)d.a, (const T*)d.f, d.g, c, d.tg, I, J, K, ring);
+    else
+      gs_column_body<T, Ar, false, TX, TY>((T*)d.a, nullptr, d.g, c, d.tg, I, J, K, ring);
+    // the body ended with a barrier after its last writes: they precede the release
+    if (lead && q != run.poison) {
+      __threadfence();
+      st_release(run.flags + df_flag(d, I, J, K, p), 1u);
+    }
+  }
 }
 
 template <typename T, class Ar, bool HAS_F, int TX, int TY>
@@ -159,18 +215,70 @@ static int gs_column_levels(stencil_ctx* ctx, T* u, const T* f, const Geom& g, C
   return STENCIL_OK;
 }
 
+template <typename T, class Ar, int TX, int TY>
+static int df_column_launch_t(stencil_ctx* ctx, const DFRun& run, cudaStream_t st) {
+  auto kern = dataflow_column_kernel<T, Ar, TX, TY>;
+  const size_t smem = col_smem_bytes<T, TX, TY>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "dataflow_column_kernel shared memory");
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, smem);
+  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+  long long blocks = (long long)ctx->sm_count * per_sm;
+  if (blocks > run.ntasks) blocks = run.ntasks > 0 ? run.ntasks : 1;
+  kern<<<(unsigned)blocks, dim3(TX, TY), smem, st>>>(run);
+  ctx->launches++;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "dataflow_column_kernel launch");
+  return STENCIL_OK;
+}
+
+template <typename T, class Ar>
+static int df_column_tile(stencil_ctx* ctx, const DFRun& run, int tx, int ty, cudaStream_t st) {
+  if (tx == 8 && ty == 8) return df_column_launch_t<T, Ar, 8, 8>(ctx, run, st);
+  if (tx == 8 && ty == 16) return df_column_launch_t<T, Ar, 8, 16>(ctx, run, st);
+  if (tx == 16 && ty == 8) return df_column_launch_t<T, Ar, 16, 8>(ctx, run, st);
+  return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column-march Gauss-Seidel tile %dx%d (supported 8x8, 8x16, 16x8)",
+                 tx, ty);
+}
+
+template <typename T>
+int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    if (int_adds == 1) return df_column_tile<T, ArithF64Mix<0x1Du>>(ctx, run, tx, ty, st);
+    if (int_adds == 2) return df_column_tile<T, ArithF64Mix<0x15u>>(ctx, run, tx, ty, st);
+    if (int_adds == 3) return df_column_tile<T, ArithF64Mix<0x12u>>(ctx, run, tx, ty, st);
+    if (int_adds == 4) return df_column_tile<T, ArithF64Mix<0x10u>>(ctx, run, tx, ty, st);
+    if (int_adds == 5) return df_column_tile<T, ArithF64Mix<0x00u>>(ctx, run, tx, ty, st);
+  }
+  return df_column_tile<T, typename DefaultArith<T>::type>(ctx, run, tx, ty, st);
+}
+template int df_column_launch<double>(stencil_ctx*, const DFRun&, int, int, int, cudaStream_t);
+template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, cudaStream_t);
+
 // Column-march Gauss-Seidel: tiles tx x ty columns (8x8, 8x16, 16x8; default 8x8 for FP64, whose FP64
-// pipe favours the short ramp of narrow tiles, 16x8 for FP32) x tz planes (default:
-// equal chunks of at most 100 planes, enough tasks per level to fill the GPU while the march's ramp of
-// tx + ty steps stays short against the chunk).
+// pipe favours the short ramp of narrow tiles, 16x8 for FP32) x tz planes (default: equal chunks of at
+// most 100 planes, enough tasks per level to fill the GPU while the march's ramp of tx + ty steps stays
+// short against the chunk).  persistent: one dataflow launch (blocking) instead of one launch per level.
 template <typename T, class Ar>
 int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,
-                  int nsweeps, cudaStream_t st) {
+                  int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st) {
   if (tx == 0) tx = sizeof(T) == 8 ? 8 : 16;
   if (ty == 0) ty = 8;
   if (tz <= 0) {
     const int chunks = (g.nz + 99) / 100;
     tz = (g.nz + chunks - 1) / chunks;
+  }
+  if (persistent) {
+    if (!((tx == 8 && (ty == 8 || ty == 16)) || (tx == 16 && ty == 8)))
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED,
+                     "column-march Gauss-Seidel tile %dx%d (supported 8x8, 8x16, 16x8)", tx, ty);
+    T* const a[1] = {u};
+    const T* const fs[1] = {f};
+    const int ns[1] = {nsweeps};
+    const double hs[1] = {h};
+    return dataflow_run<T>(ctx, DF_KIND_GS_COLUMN, 1, a, nullptr, fs, &g, ns, hs, tx, ty, tz, 1, ctx->df_timeout_ns,
+                           ctx->df_poison, st, (double)c.b, int_adds);
   }
 #define GS_COL(TXX, TYY)                                                                     \
   if (tx == TXX && ty == TYY)                                                                \
@@ -184,19 +292,19 @@ int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, 
                  tx, ty);
 }
 
-template int gs_column_run<double, ArithF64Fma>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>,
-                                                int, int, int, int, cudaStream_t);
-template int gs_column_run<double, ArithF64Mix<0x1Du>>(stencil_ctx*, double*, const double*, const Geom&,
-                                                       Coef<double>, int, int, int, int, cudaStream_t);
-template int gs_column_run<double, ArithF64Mix<0x15u>>(stencil_ctx*, double*, const double*, const Geom&,
-                                                       Coef<double>, int, int, int, int, cudaStream_t);
-template int gs_column_run<double, ArithF64Mix<0x12u>>(stencil_ctx*, double*, const double*, const Geom&,
-                                                       Coef<double>, int, int, int, int, cudaStream_t);
-template int gs_column_run<double, ArithF64Mix<0x10u>>(stencil_ctx*, double*, const double*, const Geom&,
-                                                       Coef<double>, int, int, int, int, cudaStream_t);
-template int gs_column_run<double, ArithF64Mix<0x00u>>(stencil_ctx*, double*, const double*, const Geom&,
-                                                       Coef<double>, int, int, int, int, cudaStream_t);
+template int gs_column_run<double, ArithF64Fma>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
+                                  int, int, bool, int, double, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x1Du>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
+                                  int, int, bool, int, double, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x15u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
+                                  int, int, bool, int, double, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x12u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
+                                  int, int, bool, int, double, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x10u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
+                                  int, int, bool, int, double, cudaStream_t);
+template int gs_column_run<double, ArithF64Mix<0x00u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
+                                  int, int, bool, int, double, cudaStream_t);
 template int gs_column_run<float, ArithF32>(stencil_ctx*, float*, const float*, const Geom&, Coef<float>, int, int,
-                                            int, int, cudaStream_t);
+                                  int, int, bool, int, double, cudaStream_t);
 
 }  // namespace stn

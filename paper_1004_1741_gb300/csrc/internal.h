@@ -79,7 +79,7 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
 // column-march Gauss-Seidel, one sweep per task (gs_column.cu); zero tile extents: defaults
 template <typename T, class Ar>
 int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,
-                  int nsweeps, cudaStream_t st);
+                  int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st);
 
 // Residual r = f - A u; optional FP64 r and/or FP32 r32 on the interior;
 // sums of r^2 and f^2 into the context's result slot (device) when
@@ -104,6 +104,13 @@ void dataflow_release(stencil_ctx* ctx);  // internal: no kernel instantiated fo
 template <typename T>
 int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, const T* const* f, const Geom* geoms,
                  const int* nsweeps, const double* h, int W, int H, int D, int nt, long long timeout_ns,
-                 long long poison, cudaStream_t st);
+                 long long poison, cudaStream_t st, double bco = 1.0 / 6.0, int int_adds = 0);
+// task kind of dataflow_run beside STENCIL_JACOBI / STENCIL_GS: the column-march
+// Gauss-Seidel task (gs_column.cu; nt = 1, tile W x H columns x D planes)
+constexpr int DF_KIND_GS_COLUMN = 16;
+struct DFRun;
+// launch of the persistent column-march kernel for one dataflow run (gs_column.cu)
+template <typename T>
+int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, cudaStream_t st);
 
 }  // namespace stn

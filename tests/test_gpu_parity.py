@@ -163,12 +163,12 @@ def test_gs_f64_tiles_temporal(ctx, tile, nt, variant):
 @pytest.mark.parametrize("dims", RAGGED + [(45, 38, 29), (70, 9, 33), (20, 20, 2), (17, 18, 3)])
 @pytest.mark.parametrize("tile", [(0, 0, 0), (16, 8, 0), (8, 16, 0), (16, 8, 7), (8, 8, 13), (8, 16, 40), (8, 8, 1),
                                   (16, 8, 2), (8, 8, 1000)])
-@pytest.mark.parametrize("variant", [4])
+@pytest.mark.parametrize("variant", [4, 5])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_gs_column_march(ctx, dims, tile, variant, dtype):
-    """variant 4: one thread per column marching up the tile-local wavefront, chunked or whole
-    columns (odd chunks, chunks of one plane), ragged tiles, odd and even sweep counts, with and
-    without f."""
+    """variants 4 / 5 (one launch per level / one persistent dataflow launch): one thread per
+    column marching up the tile-local wavefront, chunked or whole columns (odd chunks, chunks of
+    one plane), ragged tiles, odd and even sweep counts, with and without f."""
     u0, f0 = W.random_grid(*dims, seed=11, dtype=dtype, with_f=True)
     for ns, ff in ((1, f0), (4, None), (7, f0)):
         _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, ff, 0.04, ns, tile=tile, variant=variant),
@@ -176,7 +176,7 @@ def test_gs_column_march(ctx, dims, tile, variant, dtype):
 
 
 @pytest.mark.parametrize("int_adds", [0, 1, 2, 3, 4, 5])
-@pytest.mark.parametrize("variant", [4])
+@pytest.mark.parametrize("variant", [4, 5])
 def test_gs_column_int_adds(ctx, int_adds, variant):
     """Every integer-pipe share of the column march gives the oracle's bits (Laplace field, where
     the integer path is taken, and a random field with f)."""
@@ -196,7 +196,11 @@ def test_gs_column_rejects_nt(ctx):
     with pytest.raises(capi.StencilError):
         capi.stencil_gs_lex(ctx, u, None, 1.0, 4, tile=(32, 16, 0), variant=4)
     with pytest.raises(capi.StencilError):
-        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, variant=5)
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, tile=(32, 16, 0), variant=5)
+    with pytest.raises(capi.StencilError):
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, nt=2, variant=5)
+    with pytest.raises(capi.StencilError):
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, variant=6)
 
 
 @pytest.mark.parametrize("nt", [1, 4, 8])
@@ -277,18 +281,21 @@ def test_batched_uneven_grids(ctx, smoother, dtype, nt):
         _assert_exact(us[i].cpu().numpy(), ofn(u0, f0, h, ns), "batched grid %d" % i)
 
 
-def test_dataflow_wait_bound_reports_timeout():
+@pytest.mark.parametrize("variant", [3, 5])
+def test_dataflow_wait_bound_reports_timeout(variant):
     """A task whose completion is never published: the bounded waits expire, the
-    call returns STENCIL_ERR_TIMEOUT, and the context keeps working."""
+    call returns STENCIL_ERR_TIMEOUT, and the context keeps working (tile tasks
+    and column-march tasks)."""
     c = capi.Context(0)
     u0, _ = W.random_grid(40, 40, 40, seed=1)
     u = _dev(u0)
     capi.stencil_set_wait_limit(c, 50_000_000, never_publish=3)
     with pytest.raises(capi.StencilError) as e:
-        capi.stencil_gs_lex(c, u, None, 1.0, 4, variant=3)
+        capi.stencil_gs_lex(c, u, None, 1.0, 4, variant=variant)
     assert e.value.code == capi.STENCIL_ERR_TIMEOUT
     capi.stencil_set_wait_limit(c, 10_000_000_000, never_publish=-1)
-    _assert_exact(_run(c, capi.stencil_gs_lex, u0, None, 1.0, 4, variant=3), oracle.gs_lex(u0, None, 1.0, 4), "after")
+    _assert_exact(_run(c, capi.stencil_gs_lex, u0, None, 1.0, 4, variant=variant), oracle.gs_lex(u0, None, 1.0, 4),
+                  "after")
     c.close()
 
 
