@@ -47,10 +47,19 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 ALU peak derived from the unit counts and clock: 152 SMs x 2 FP64 lanes per
+# FP64 pipe peak derived from the unit counts and clock: 152 SMs x 2 FP64 lanes per
 # clock x 2070 MHz = 629.3 G FP64 operations/s (the 1.25 TFLOP/s datasheet figure
 # counts an FMA as two).  Each add or multiply of the site update is one operation.
 FP64_ALU_PEAK_TOPS = 152 * 2 * 2.070e9 / 1e12
+# The kernels also run binary64 additions on the integer ALU pipe (64 lanes per clock
+# per SM, ncu sm__inst_executed_pipe_alu.avg.peak_sustained = 2 warp instructions per
+# cycle), each costing INT_ADD_ALU_INSTR ALU warp instructions per warp of additions
+# (ncu: the Jacobi z-march executes 20.0 ALU warp instructions per warp of sites with
+# no integer additions and 117.4 with three).  With the multiply on the FP64 pipe and
+# the five additions split freely, the two pipes together retire at most
+# (2 + 64 / INT_ADD_ALU_INSTR) operations per clock per SM: the bound reported below.
+INT_ADD_ALU_INSTR = (117.4 - 20.0) / 3
+FP64_COMBINED_PEAK_TOPS = 152 * (2 + 64 / INT_ADD_ALU_INSTR) * 2.070e9 / 1e12
 
 
 class ClockSampler:
@@ -284,19 +293,22 @@ def run_gpu(args):
     flops_per_launch = FP64_OPS_PER_LUP * SWEEPS * N ** 3 / nlaunch
     achieved = flops_per_launch / dur_s / 1e12
     traffic = _traffic_from_profiles(kern)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK_TOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_ALU_PEAK_TOPS, "traffic": traffic, "kernel": kern,
-                "peak_source": "derived: 152 SM x 2 FP64 lanes/clk x 2070 MHz (1.25 TFLOP/s FMA-counted datasheet); "
-                               "achieved counts the 6 FP64 operations of a site update, some of which run on the "
-                               "integer pipes"}
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_COMBINED_PEAK_TOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_COMBINED_PEAK_TOPS, "traffic": traffic, "kernel": kern,
+                "peak_source": "derived: 152 SM x (2 FP64 lanes/clk + 64 integer ALU lanes/clk / %.1f ALU "
+                               "instructions per integer-pipe binary64 add, ncu) x 2070 MHz; achieved counts the 6 "
+                               "algorithmic FP64 operations of a site update (5 adds, 1 multiply)"
+                               % INT_ADD_ALU_INSTR,
+                "frac_of_fp64_pipe_only": achieved / FP64_ALU_PEAK_TOPS}
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_bound = {str(nt): hbm * nt / 16.0 for nt in NT_SWEEP}
 
     details = {"glups": glups, "hbm_roofline_glups_fp64": hbm_bound, "hbm_gbs": hbm, "hbm_source": src,
-               "fp64_alu_roofline_glups": FP64_ALU_PEAK_TOPS * 1e12 / FP64_OPS_PER_LUP / 1e9,
+               "fp64_pipe_roofline_glups": FP64_ALU_PEAK_TOPS * 1e12 / FP64_OPS_PER_LUP / 1e9,
+               "fp64_plus_int_roofline_glups": FP64_COMBINED_PEAK_TOPS * 1e12 / FP64_OPS_PER_LUP / 1e9,
                "frac_of_min_roofline": {k: v / min(hbm / 16.0 * HEADLINE[k]["nt"],
-                                                   FP64_ALU_PEAK_TOPS * 1e3 / FP64_OPS_PER_LUP)
+                                                   FP64_COMBINED_PEAK_TOPS * 1e3 / FP64_OPS_PER_LUP)
                                         for k, v in glups.items()}}
 
     # temporal depth sweep (one 100-sweep run per nt and smoother, after the timed region)

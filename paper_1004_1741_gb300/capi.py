@@ -283,7 +283,7 @@ def residual_norm(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: floa
 
 
 def stencil_batched(ctx: Context, us, fs, hs, nsweeps, smoother: int, *, nt: int = 0, tile=(0, 0, 0),
-                    stream=None) -> None:
+                    variant: int = 0, int_adds: int = -1, stream=None) -> None:
     """Smooth many grids (a list of tensors, one dtype) in one persistent launch."""
     lib = load_library()
     n = len(us)
@@ -301,7 +301,7 @@ def stencil_batched(ctx: Context, us, fs, hs, nsweeps, smoother: int, *, nt: int
         dims[3 * i], dims[3 * i + 1], dims[3 * i + 2] = d[0], d[1], d[2]
     hh = (ctypes.c_double * n)(*[float(x) for x in hs])
     ns = (ctypes.c_int * n)(*[int(x) for x in nsweeps])
-    p = _params(nt, tile)
+    p = _params(nt, tile, variant=variant, int_adds=int_adds)
     rc = lib.stencil_batched(ctx.handle, n, up, fp, dims, hh, ns, int(smoother), dtype, ctypes.byref(p),
                              _stream(stream))
     _check(ctx, rc)

@@ -219,7 +219,7 @@ int stencil_solve_mixed(stencil_ctx* ctx, double* u, const double* f, const int6
     e = cudaMemsetAsync(e32, 0, n * sizeof(float), st);
     if (e != cudaSuccess) return cuda_err(ctx, e, "memset e32");
     // FP32 inner sweeps: Jacobi with on-chip temporal blocking (3 sweeps per
-    // pass), Gauss-Seidel as the column march (one sweep per task)
+    // pass), Gauss-Seidel as the persistent column march (one sweep per task)
     stencil_params q{};
     q.int_adds = -1;
     if (smoother == STENCIL_JACOBI) {
@@ -230,7 +230,7 @@ int stencil_solve_mixed(stencil_ctx* ctx, double* u, const double* f, const int6
       rc = jacobi_run<float>(ctx, e32, r32, g, h, inner_sweeps, &q, st);
     } else {
       q.nt = 1;
-      q.variant = 4;
+      q.variant = 5;
       rc = gs_run<float>(ctx, e32, r32, g, h, inner_sweeps, &q, st);
     }
     if (rc) return rc;
