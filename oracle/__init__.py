@@ -24,6 +24,13 @@ Functions and what pins them (see ``tests/test_oracle_pins.py``):
   ``A phi = lambda phi`` and the sparse matrix form; its norm by ``math.fsum``.
 * ``solve_mixed`` / ``solve_f64`` (not in the paper): pinned by the closed-form
   solution ``u* = sum a_m phi_m / lambda_m``.
+* ``mg_restrict`` / ``mg_prolong_add`` / ``mg_solve`` (multigrid, named in Sec. 1
+  and Sec. 3 as the setting of these smoothers; transfers are the textbook full
+  weighting and trilinear interpolation): pinned by exact reproduction of linear
+  functions by both transfers, by the restriction's weights summing to one, by
+  the V-cycle's reduction factor on the error of the discrete Laplace problem,
+  by convergence to the closed-form discrete solution, and by the one-level
+  cycle reducing to plain smoothing sweeps.
 """
 from __future__ import annotations
 
@@ -57,8 +64,12 @@ def _lib():
         lib.oracle_gs_lex_f32.argtypes = [_P, _P, _I64, _I64, _I64, _D, _F, _I]
         lib.oracle_solve_mixed.argtypes = [_P, _P, _I64, _I64, _I64, _D, _I, _D, _I, _I, _P, _P]
         lib.oracle_solve_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _I, _D, _I, _I, _P, _P]
+        lib.oracle_mg_restrict_f64.argtypes = [_P, _I64, _I64, _I64, _P]
+        lib.oracle_mg_prolong_add_f64.argtypes = [_P, _I64, _I64, _I64, _P]
+        lib.oracle_mg_solve_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _I, _I, _I, _I, _I, _D, _I, _P, _P]
         for name in ("oracle_jacobi_f64", "oracle_gs_lex_f64", "oracle_gs_rb_f64", "oracle_gs_rb_f32", "oracle_residual_f64",
-                     "oracle_jacobi_f32", "oracle_gs_lex_f32", "oracle_solve_mixed", "oracle_solve_f64"):
+                     "oracle_jacobi_f32", "oracle_gs_lex_f32", "oracle_solve_mixed", "oracle_solve_f64",
+                     "oracle_mg_restrict_f64", "oracle_mg_prolong_add_f64", "oracle_mg_solve_f64"):
             getattr(lib, name).restype = _I
         _LIB = lib
     return _LIB
@@ -178,3 +189,48 @@ def solve_f64(u: np.ndarray, f: np.ndarray | None, h: float, smoother: int, rtol
     if rc not in (0, -5):
         raise RuntimeError("oracle_solve_f64 rc=%d" % rc)
     return out, rel.value, sw.value, rc == 0
+
+
+MG_JACOBI = 0  # weighted Jacobi, omega = 6/7 (a = b = 1/7)
+MG_GS = 1      # lexicographic Gauss-Seidel
+
+
+def mg_restrict(r: np.ndarray) -> np.ndarray:
+    """Full-weighting restriction of the interior of r (odd extents) to the coarse
+    grid of extents (n-1)/2 (zero halo)."""
+    _check(r, None, np.float64)
+    nx, ny, nz = _dims(r)
+    fc = np.zeros(((nz - 1) // 2 + 2, (ny - 1) // 2 + 2, (nx - 1) // 2 + 2))
+    rc = _lib().oracle_mg_restrict_f64(_ptr(r), nx, ny, nz, _ptr(fc))
+    if rc != 0:
+        raise RuntimeError("oracle_mg_restrict_f64 rc=%d" % rc)
+    return fc
+
+
+def mg_prolong_add(u: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """u plus the trilinear prolongation of the coarse correction e (zero on the
+    coarse boundary); u is not modified."""
+    out = np.array(u, copy=True, order="C")
+    _check(out, None, np.float64)
+    _check(e, None, np.float64)
+    nx, ny, nz = _dims(out)
+    if _dims(e) != ((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2):
+        raise ValueError("e must be the coarse grid of u")
+    rc = _lib().oracle_mg_prolong_add_f64(_ptr(out), nx, ny, nz, _ptr(e))
+    if rc != 0:
+        raise RuntimeError("oracle_mg_prolong_add_f64 rc=%d" % rc)
+    return out
+
+
+def mg_solve(u: np.ndarray, f: np.ndarray | None, h: float, smoother: int, nu1: int, nu2: int, ncoarse: int,
+             max_levels: int, rtol: float, max_cycles: int):
+    """Multigrid V-cycles until rel <= rtol or max_cycles.  Returns (u, rel, cycles, converged)."""
+    out = np.array(u, copy=True, order="C")
+    _check(out, f, np.float64)
+    rel = ctypes.c_double(0.0)
+    cyc = ctypes.c_int(0)
+    rc = _lib().oracle_mg_solve_f64(_ptr(out), _ptr(f), *_dims(out), h, smoother, nu1, nu2, ncoarse, max_levels,
+                                    rtol, max_cycles, ctypes.addressof(rel), ctypes.addressof(cyc))
+    if rc not in (0, -5):
+        raise RuntimeError("oracle_mg_solve_f64 rc=%d" % rc)
+    return out, rel.value, cyc.value, rc == 0

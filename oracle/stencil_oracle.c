@@ -358,3 +358,178 @@ int oracle_solve_f64(double* u, const double* f, int64_t nx, int64_t ny, int64_t
   if (out_sweeps) *out_sweeps = done;
   return rel <= rtol ? ORC_OK : ORC_NOT_CONVERGED;
 }
+
+/* ---------------------------------------------------------------------------
+ * Multigrid V-cycle with these smoothers (Sec. 1 and Sec. 3 name multigrid
+ * solvers as the place where the smoothers spend their time; the grid
+ * transfers below are the textbook ones, written out in a fixed order).
+ *
+ * Levels: level 0 is the given grid; while fewer than max_levels levels exist
+ * and every extent of the last one is odd and >= 3, the next level has
+ * extents (n-1)/2 and spacing 2h.  Coarse site I sits on fine site 2I+1
+ * (0-based interior coordinates), so every fine neighbour of a coarse site is
+ * interior.
+ *
+ * Smoothers: 0 = weighted Jacobi with omega = 6/7 (a = 1 - omega = 1/7,
+ * b = omega/6 = 1/7), 1 = lexicographic Gauss-Seidel (b = 1/6).
+ *
+ * Restriction (full weighting, weights 1/4, 1/2, 1/4 per axis), in this order:
+ *   along x:  sx = (0.25*r[i-1] + 0.5*r[i]) + 0.25*r[i+1]
+ *   along y:  sy = (0.25*sx[j-1] + 0.5*sx[j]) + 0.25*sx[j+1]
+ *   along z:  fc = (0.25*sy[k-1] + 0.5*sy[k]) + 0.25*sy[k+1]
+ * Prolongation (trilinear, zero on the coarse boundary), added to u:
+ *   per axis, an odd fine index takes its coarse site, an even one the mean
+ *   (a + b) * 0.5 of the two coarse sites around it; x first, then y, then z.
+ *
+ * V-cycle at level l < L-1: nu1 smoothing sweeps; r = f - A u (the residual
+ * above); f_{l+1} = restriction of r; u_{l+1} = 0 (halo included: the error
+ * has zero Dirichlet values); V-cycle at l+1; u_l += prolongation of u_{l+1};
+ * nu2 smoothing sweeps.  At the coarsest level: ncoarse sweeps.
+ *
+ * Solve: rel = ||r||/||f|| (||r0|| if f == 0) before and after each cycle;
+ * cycles while rel > rtol and fewer than max_cycles cycles ran.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  orc_grid g;
+  double h;
+  double* u; /* level > 0: the correction */
+  double* f; /* level > 0: the restricted residual */
+  double* r;
+} orc_level;
+
+static void orc_mg_smooth(orc_level* L, int smoother, int nsweeps) {
+  if (nsweeps <= 0) return;
+  if (smoother == 0)
+    oracle_jacobi_f64(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, 1.0 / 7.0, 1.0 / 7.0, nsweeps);
+  else
+    oracle_gs_lex_f64(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, 1.0 / 6.0, nsweeps);
+}
+
+/* fc (coarse interior) = full weighting of r (fine interior). */
+int oracle_mg_restrict_f64(const double* r, int64_t nx, int64_t ny, int64_t nz, double* fc) {
+  orc_grid gf, gc;
+  if (!r || !fc || orc_grid_make(&gf, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  if (nx % 2 == 0 || ny % 2 == 0 || nz % 2 == 0) return ORC_ERR_ARG;
+  orc_grid_make(&gc, (nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2);
+  for (int64_t K = 0; K < gc.nz; ++K)
+    for (int64_t J = 0; J < gc.ny; ++J)
+      for (int64_t I = 0; I < gc.nx; ++I) {
+        double sy[3];
+        for (int dz = -1; dz <= 1; ++dz) {
+          double sx[3];
+          for (int dy = -1; dy <= 1; ++dy) {
+            size_t c = orc_at(&gf, 2 * I + 1, 2 * J + 1 + dy, 2 * K + 1 + dz);
+            sx[dy + 1] = (0.25 * r[c - 1] + 0.5 * r[c]) + 0.25 * r[c + 1];
+          }
+          sy[dz + 1] = (0.25 * sx[0] + 0.5 * sx[1]) + 0.25 * sx[2];
+        }
+        fc[orc_at(&gc, I, J, K)] = (0.25 * sy[0] + 0.5 * sy[1]) + 0.25 * sy[2];
+      }
+  return ORC_OK;
+}
+
+/* u (fine interior) += trilinear prolongation of e (coarse, zero halo). */
+int oracle_mg_prolong_add_f64(double* u, int64_t nx, int64_t ny, int64_t nz, const double* e) {
+  orc_grid gf, gc;
+  if (!u || !e || orc_grid_make(&gf, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  if (nx % 2 == 0 || ny % 2 == 0 || nz % 2 == 0) return ORC_ERR_ARG;
+  orc_grid_make(&gc, (nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2);
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        /* coarse interior coordinates around (i, j, k); -1 and n_c are the zero halo */
+        const int64_t xa = (i % 2) ? (i - 1) / 2 : i / 2 - 1, xb = (i % 2) ? xa : i / 2;
+        const int64_t ya = (j % 2) ? (j - 1) / 2 : j / 2 - 1, yb = (j % 2) ? ya : j / 2;
+        const int64_t za = (k % 2) ? (k - 1) / 2 : k / 2 - 1, zb = (k % 2) ? za : k / 2;
+        double ey[2];
+        for (int zz = 0; zz < 2; ++zz) {
+          const int64_t Z = zz ? zb : za;
+          double ex[2];
+          for (int yy = 0; yy < 2; ++yy) {
+            const int64_t Y = yy ? yb : ya;
+            const double a = e[orc_at(&gc, xa, Y, Z)];
+            ex[yy] = (i % 2) ? a : (a + e[orc_at(&gc, xb, Y, Z)]) * 0.5;
+          }
+          ey[zz] = (j % 2) ? ex[0] : (ex[0] + ex[1]) * 0.5;
+        }
+        const double ez = (k % 2) ? ey[0] : (ey[0] + ey[1]) * 0.5;
+        const size_t c = orc_at(&gf, i, j, k);
+        u[c] = u[c] + ez;
+      }
+  return ORC_OK;
+}
+
+static void orc_vcycle(orc_level* lv, int l, int nlev, int smoother, int nu1, int nu2, int ncoarse) {
+  orc_level* L = &lv[l];
+  if (l == nlev - 1) {
+    orc_mg_smooth(L, smoother, ncoarse);
+    return;
+  }
+  orc_level* C = &lv[l + 1];
+  orc_mg_smooth(L, smoother, nu1);
+  double rn;
+  oracle_residual_f64(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, L->r, &rn, NULL);
+  oracle_mg_restrict_f64(L->r, L->g.nx, L->g.ny, L->g.nz, C->f);
+  memset(C->u, 0, orc_total(&C->g) * sizeof(double));
+  orc_vcycle(lv, l + 1, nlev, smoother, nu1, nu2, ncoarse);
+  oracle_mg_prolong_add_f64(L->u, L->g.nx, L->g.ny, L->g.nz, C->u);
+  orc_mg_smooth(L, smoother, nu2);
+}
+
+int oracle_mg_solve_f64(double* u, const double* f, int64_t nx, int64_t ny, int64_t nz, double h, int smoother,
+                        int nu1, int nu2, int ncoarse, int max_levels, double rtol, int max_cycles, double* out_rel,
+                        int* out_cycles) {
+  orc_grid g0;
+  if (!u || orc_grid_make(&g0, nx, ny, nz) != ORC_OK || !(h > 0.0) || (smoother != 0 && smoother != 1) ||
+      nu1 < 0 || nu2 < 0 || ncoarse < 0 || max_levels < 1 || max_levels > 32 || max_cycles < 0)
+    return ORC_ERR_ARG;
+  orc_level lv[32];
+  memset(lv, 0, sizeof(lv));
+  int nlev = 1;
+  lv[0].g = g0;
+  lv[0].h = h;
+  lv[0].u = u;
+  lv[0].f = (double*)f;
+  while (nlev < max_levels) {
+    const orc_grid* p = &lv[nlev - 1].g;
+    if (p->nx < 3 || p->ny < 3 || p->nz < 3 || p->nx % 2 == 0 || p->ny % 2 == 0 || p->nz % 2 == 0) break;
+    orc_grid_make(&lv[nlev].g, (p->nx - 1) / 2, (p->ny - 1) / 2, (p->nz - 1) / 2);
+    lv[nlev].h = 2.0 * lv[nlev - 1].h;
+    ++nlev;
+  }
+  int rc = ORC_OK;
+  for (int l = 0; l < nlev; ++l) {
+    const size_t n = orc_total(&lv[l].g);
+    lv[l].r = (double*)calloc(n, sizeof(double));
+    if (l > 0) {
+      lv[l].u = (double*)calloc(n, sizeof(double));
+      lv[l].f = (double*)calloc(n, sizeof(double));
+    }
+    if (!lv[l].r || (l > 0 && (!lv[l].u || !lv[l].f))) rc = ORC_ERR_OOM;
+  }
+  double rel = 0.0;
+  int it = 0;
+  if (rc == ORC_OK) {
+    double rn = 0.0, fn = 0.0;
+    oracle_residual_f64(u, f, nx, ny, nz, h, NULL, &rn, &fn);
+    const double denom = fn > 0.0 ? fn : rn;
+    rel = denom > 0.0 ? rn / denom : 0.0;
+    while (rel > rtol && it < max_cycles) {
+      orc_vcycle(lv, 0, nlev, smoother, nu1, nu2, ncoarse);
+      ++it;
+      oracle_residual_f64(u, f, nx, ny, nz, h, NULL, &rn, NULL);
+      rel = denom > 0.0 ? rn / denom : 0.0;
+    }
+  }
+  for (int l = 0; l < nlev; ++l) {
+    free(lv[l].r);
+    if (l > 0) {
+      free(lv[l].u);
+      free(lv[l].f);
+    }
+  }
+  if (rc != ORC_OK) return rc;
+  if (out_rel) *out_rel = rel;
+  if (out_cycles) *out_cycles = it;
+  return rel <= rtol ? ORC_OK : ORC_NOT_CONVERGED;
+}

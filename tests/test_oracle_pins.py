@@ -391,3 +391,132 @@ def test_dataflow_dependency_rule_is_sharp():
     finally:
         S.dataflow_deps = orig
     assert broken > 0
+
+
+# -------------------------------------------------------------- multigrid ----
+def _padded(nx, ny, nz):
+    return np.zeros((nz + 2, ny + 2, nx + 2))
+
+
+def _fill_interior(a, fn):
+    nz, ny, nx = (s - 2 for s in a.shape)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    a[1:-1, 1:-1, 1:-1] = fn(i, j, k)
+    return a
+
+
+@pytest.mark.parametrize("dims", [(7, 5, 9), (5, 5, 5), (11, 3, 7)])
+def test_mg_restriction_reproduces_linear_functions(dims):
+    """Full weighting is exact for linear functions and its weights sum to one:
+    the coarse value equals the fine value at the coarse site's fine position
+    (2I+1, 2J+1, 2K+1), for a constant and for each axis separately."""
+    nx, ny, nz = dims
+    for fn in (lambda i, j, k: 0 * i + 3.0, lambda i, j, k: 2.0 * i - 1.0, lambda i, j, k: 3.0 * j + 0.5,
+               lambda i, j, k: -4.0 * k + 2.0, lambda i, j, k: i + 2.0 * j - 3.0 * k):
+        r = _fill_interior(_padded(nx, ny, nz), fn)
+        fc = oracle.mg_restrict(r)
+        want = _fill_interior(_padded((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2),
+                              lambda I, J, K: fn(2 * I + 1, 2 * J + 1, 2 * K + 1))
+        np.testing.assert_array_equal(fc, want)
+
+
+def test_mg_restriction_weights_by_position():
+    """A unit value at each of the 27 fine sites around a coarse site: every
+    coarse site C receives the product over the axes of w(fine - (2C+1)), with
+    w(0) = 1/2, w(+-1) = 1/4 and 0 beyond (a transposed axis, a dropped term or
+    a wrong weight changes one of the 27 images)."""
+    nx, ny, nz = 7, 9, 5
+    I, J, K = 1, 2, 1
+    w1 = lambda d: np.where(d == 0, 0.5, np.where(np.abs(d) == 1, 0.25, 0.0))
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                fi, fj, fk = 2 * I + 1 + dx, 2 * J + 1 + dy, 2 * K + 1 + dz
+                r = _padded(nx, ny, nz)
+                r[fk + 1, fj + 1, fi + 1] = 1.0
+                fc = oracle.mg_restrict(r)
+                want = _fill_interior(_padded((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2),
+                                      lambda Ic, Jc, Kc: w1(fi - (2 * Ic + 1)) * w1(fj - (2 * Jc + 1)) *
+                                      w1(fk - (2 * Kc + 1)))
+                np.testing.assert_array_equal(fc, want)
+                assert fc[K + 1, J + 1, I + 1] == 0.5 ** (3 + abs(dx) + abs(dy) + abs(dz))
+
+
+@pytest.mark.parametrize("dims", [(9, 7, 11), (5, 5, 5)])
+def test_mg_prolongation_reproduces_linear_functions(dims):
+    """Trilinear interpolation is exact for linear functions away from the
+    boundary (whose coarse values are the zero halo): a coarse linear function
+    comes back as the same function on the fine sites between coarse sites."""
+    nx, ny, nz = dims
+    g = lambda i, j, k: 0.5 * i - 2.0 * j + 3.0 * k + 1.25
+    e = _fill_interior(_padded((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2),
+                       lambda I, J, K: g(2 * I + 1, 2 * J + 1, 2 * K + 1))
+    u = oracle.mg_prolong_add(_padded(nx, ny, nz), e)
+    want = _fill_interior(_padded(nx, ny, nz), g)
+    np.testing.assert_array_equal(u[2:-2, 2:-2, 2:-2], want[2:-2, 2:-2, 2:-2])
+    # added, not assigned: a second application doubles it
+    u2 = oracle.mg_prolong_add(u, e)
+    np.testing.assert_array_equal(u2[2:-2, 2:-2, 2:-2], 2 * want[2:-2, 2:-2, 2:-2])
+
+
+def test_mg_prolongation_of_a_spike_is_the_hat_function():
+    """A unit coarse value at (I,J,K) spreads as the product of 1D hats
+    (1 at 2I+1, 1/2 at 2I and 2I+2), zero elsewhere; near the boundary the
+    missing coarse neighbour is the zero halo."""
+    nx, ny, nz = 9, 7, 5
+    for I, J, K in ((1, 1, 0), (0, 2, 1), (3, 0, 1)):
+        e = _padded((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2)
+        e[K + 1, J + 1, I + 1] = 1.0
+        u = oracle.mg_prolong_add(_padded(nx, ny, nz), e)
+        hat = lambda x, c: np.maximum(0.0, 1.0 - np.abs(x - c) / 2.0)
+        want = _fill_interior(_padded(nx, ny, nz),
+                              lambda i, j, k: hat(i, 2 * I + 1) * hat(j, 2 * J + 1) * hat(k, 2 * K + 1))
+        np.testing.assert_array_equal(u, want)
+
+
+@pytest.mark.parametrize("smoother,bound", [(oracle.MG_GS, 0.2), (oracle.MG_JACOBI, 0.32)])
+def test_mg_vcycle_reduces_the_error_by_a_fixed_factor(smoother, bound):
+    """Laplace problem with zero Dirichlet data (solution 0) from a random start:
+    every V(2,2) cycle shrinks the error by a grid-independent factor (textbook
+    multigrid; ~0.15 for Gauss-Seidel, ~0.27 for Jacobi with omega = 6/7).  A
+    wrong sign of the correction, a wrong h scaling of a coarse level or a
+    transfer that is not a weighted mean stalls or diverges."""
+    rng = np.random.default_rng(7)
+    for n in (15, 31):
+        u = _padded(n, n, n)
+        u[1:-1, 1:-1, 1:-1] = rng.random((n, n, n))
+        prev = np.abs(u).max()
+        for _ in range(4):
+            u, _, _, _ = oracle.mg_solve(u, None, 1.0 / (n + 1), smoother, 2, 2, 10, 8, 0.0, 1)
+            cur = np.abs(u).max()
+            assert cur <= bound * prev
+            prev = cur
+
+
+@pytest.mark.parametrize("smoother", [oracle.MG_GS, oracle.MG_JACOBI])
+def test_mg_solve_reaches_closed_form(smoother):
+    """f a sum of sine modes: the V-cycles converge to u* = sum a phi / lambda
+    (the discrete solution, to rounding) within a handful of cycles."""
+    n = 31
+    h, f, ustar = _sine_rhs(n, [(1, 1, 1), (2, 1, 3), (5, 7, 2)], [1.0, -0.7, 0.4])
+    u, rel, cycles, ok = oracle.mg_solve(np.zeros_like(f), f, h, smoother, 2, 2, 20, 8, 1e-11, 40)
+    assert ok and rel <= 1e-11
+    assert cycles <= (15 if smoother == oracle.MG_GS else 25)
+    assert np.abs(u - ustar).max() <= 1e-9 * np.abs(ustar).max()
+
+
+def test_mg_one_level_is_plain_smoothing():
+    """With one level (max_levels = 1, or an even extent that cannot coarsen) a
+    cycle is ncoarse sweeps of the smoother: Gauss-Seidel, and Jacobi with
+    a = b = 1/7."""
+    rng = np.random.default_rng(3)
+    for dims, levels in (((7, 5, 9), 1), ((8, 7, 7), 6)):
+        nx, ny, nz = dims
+        u0 = rng.random((nz + 2, ny + 2, nx + 2))
+        f = _padded(nx, ny, nz)
+        f[1:-1, 1:-1, 1:-1] = rng.standard_normal((nz, ny, nx))
+        h = 0.1
+        got, _, _, _ = oracle.mg_solve(u0, f, h, oracle.MG_GS, 3, 3, 5, levels, 0.0, 1)
+        np.testing.assert_array_equal(got, oracle.gs_lex(u0, f, h, 5))
+        got, _, _, _ = oracle.mg_solve(u0, f, h, oracle.MG_JACOBI, 3, 3, 5, levels, 0.0, 1)
+        np.testing.assert_array_equal(got, oracle.jacobi(u0, f, h, 5, a=1.0 / 7.0, b=1.0 / 7.0))
