@@ -537,6 +537,62 @@ def run_suite_mixed(args):
     return 0
 
 
+def run_suite_mg(args):
+    """Multigrid V-cycle solve of the sine-mode Poisson problem (8 modes + N(0,1e-3)
+    noise, seed 4) at 511^3 (odd extents: 8 levels down to 1^3) to a relative
+    residual of 1e-10 with each smoother, V(2,2), 20 coarsest sweeps; against the
+    plain FP64 sweeps of the same smoother (which need ~10^6 sweeps for 1e-10 at
+    this size: their time is projected from their measured GLUP/s) and the serial
+    oracle's time per V-cycle on a bounded 127^3 sample."""
+    import torch
+
+    import oracle
+    from paper_1004_1741_gb300 import capi, workloads
+
+    n = args.n if args.n != 320 else 511
+    prob = workloads.sine_modes_problem(n, seed=4)
+    dev = torch.device("cuda", 0)
+    ctx = capi.Context(0)
+    f = torch.from_numpy(prob.f).to(dev)
+    res = {}
+    for name, sm in (("gs", capi.STENCIL_GS), ("jacobi", capi.STENCIL_JACOBI)):
+        u = torch.zeros_like(f)
+        capi.stencil_mg_solve(ctx, u, f, prob.h, sm, rtol=0.0, max_cycles=1)  # warm (workspace, tables)
+        u.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rel, cycles, ok = capi.stencil_mg_solve(ctx, u, f, prob.h, sm, nu1=2, nu2=2, ncoarse=20, rtol=1e-10,
+                                                max_cycles=60)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        abs_r, rel_check = capi.residual_norm(ctx, u, f, prob.h)
+        # plain sweeps of the same smoother for comparison (measured rate, projected count)
+        u2 = torch.zeros_like(f)
+        rel200, sw, _ = capi.stencil_solve_f64(ctx, u2, f, prob.h, sm, 0.0, 200, 100)
+        u2.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rel200, sw, _ = capi.stencil_solve_f64(ctx, u2, f, prob.h, sm, 0.0, 200, 100)
+        torch.cuda.synchronize()
+        t_sw = time.perf_counter() - t1
+        res[name] = {"cycles": cycles, "rel": rel, "reached": ok, "s": t, "s_per_cycle": t / max(cycles, 1),
+                     "rel_check": rel_check,
+                     "fine_sweep_equivalent_glups": n ** 3 * 4 * cycles / t / 1e9,
+                     "plain_sweeps": {"sweeps": sw, "rel_after": rel200, "s": t_sw,
+                                      "glups": n ** 3 * sw / t_sw / 1e9}}
+    # CPU oracle: one V-cycle on a 127^3 sample of the same problem family
+    small = workloads.sine_modes_problem(127, seed=4)
+    t0 = time.perf_counter()
+    oracle.mg_solve(small.f * 0.0, small.f, small.h, oracle.MG_GS, 2, 2, 20, 32, 0.0, 1)
+    t_cpu = time.perf_counter() - t0
+    line = {"suite": "mg", "metric": "time to relative residual 1e-10, %d^3 Poisson, multigrid V(2,2)" % n,
+            "n": n, "unit": "s", "data": "synthetic", "results": res,
+            "cpu_oracle": {"n": 127, "smoother": "gs", "s_per_cycle": t_cpu, "cores": 1, "kind": "oracle"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_suite_served(args):
     """Served stream: Poisson arrivals of smoothing and solve requests (sides
     log-uniform in [32, 384], rounded to multiples of 16; 10-200 sweeps or a solve
@@ -621,7 +677,7 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="kernel variant of the profiling case")
     ap.add_argument("--int-adds", type=int, default=-1, help="integer-pipe additions of the profiling case")
     ap.add_argument("--repeat", type=int, default=1)
-    ap.add_argument("--suite", choices=["mixed", "served"], help="a secondary workload instead of the headline")
+    ap.add_argument("--suite", choices=["mixed", "served", "mg"], help="a secondary workload instead of the headline")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")
     ap.add_argument("--window", type=float, default=3.0)
     ap.add_argument("--drain", type=float, default=60.0)
@@ -633,6 +689,8 @@ def main():
         return run_suite_mixed(args)
     if args.suite == "served":
         return run_suite_served(args)
+    if args.suite == "mg":
+        return run_suite_mg(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -202,6 +202,31 @@ int stencil_batched(stencil_ctx* ctx, int n, void* const* u, const void* const* 
                     const double* h, const int* nsweeps, int smoother, int dtype, const stencil_params* params,
                     void* stream);
 
+/* Multigrid V-cycle solve of -Lap_h u = f (the paper's smoothers inside the
+ * solver that Sec. 1 and Sec. 3 name as their setting; the cycle itself is not
+ * in the paper and follows the textbook form).  FP64, in place on u (device),
+ * f device or NULL (f = 0), dims interior extents, h > 0.
+ *  Levels: level 0 is u's grid; while fewer than max_levels (1..32) levels
+ *    exist and every extent of the last is odd and >= 3, the next level has
+ *    extents (n-1)/2 and spacing 2h (coarse site I on fine site 2I+1).
+ *  Cycle: nu1 sweeps of the smoother, r = f - A u, full-weighting
+ *    restriction (weights 1/4, 1/2, 1/4 per axis; x, then y, then z), the
+ *    coarse correction from zero with zero Dirichlet values (one cycle deeper),
+ *    trilinear prolongation added to u (x, then y, then z), nu2 sweeps;
+ *    ncoarse sweeps on the coarsest level.
+ *  smoother: STENCIL_JACOBI = weighted Jacobi, omega = 6/7 (a = b = 1/7);
+ *    STENCIL_GS = lexicographic Gauss-Seidel (b = 1/6).
+ *  Runs cycles while ||r||/||f|| (||r0|| if f = 0) > rtol and fewer than
+ *  max_cycles ran; *out_rel, *out_cycles (host, may be NULL) get the last
+ *  relative residual and the cycles run.  Returns STENCIL_OK or
+ *  STENCIL_ERR_NOT_CONVERGED (u holds the last iterate either way).
+ *  Workspace: the coarse levels (about 2/7 of u's size) and one residual grid
+ *  of u's size, plus the smoothers' own.  Blocking (reads the residual after
+ *  every cycle).  Same bits as the serial definition. */
+int stencil_mg_solve(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h, int smoother,
+                     int nu1, int nu2, int ncoarse, int max_levels, double rtol, int max_cycles, double* out_rel,
+                     int* out_cycles, void* stream);
+
 /* Bound on every device-side wait of the persistent kernels (default 10 s).
  * never_publish >= 0 makes the task at that queue index never publish its
  * completion, so that a test can watch the bound expire and the error come

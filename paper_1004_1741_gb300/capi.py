@@ -111,6 +111,8 @@ _SIGS = {
     "stencil_solve_mixed": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
     "stencil_solve_f64": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, _PP, ctypes.POINTER(_D), ctypes.POINTER(_I),
                                _P]),
+    "stencil_mg_solve": (_I, [_P, _P, _P, _I64P, _D, _I, _I, _I, _I, _I, _D, _I, ctypes.POINTER(_D),
+                              ctypes.POINTER(_I), _P]),
 }
 
 _LIB = None
@@ -369,6 +371,19 @@ def stencil_solve_f64(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: 
                                ctypes.byref(p), ctypes.byref(rel), ctypes.byref(sw), _stream(stream))
     _check(ctx, rc, allow=(STENCIL_ERR_NOT_CONVERGED,))
     return rel.value, sw.value, rc == STENCIL_OK
+
+
+def stencil_mg_solve(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, smoother: int, *,
+                     nu1: int = 2, nu2: int = 2, ncoarse: int = 20, max_levels: int = 32, rtol: float = 1e-10,
+                     max_cycles: int = 50, stream=None):
+    """Multigrid V-cycles (FP64) until the relative residual <= rtol; returns (rel, cycles, converged)."""
+    lib = load_library()
+    rel, cyc = ctypes.c_double(0.0), ctypes.c_int(0)
+    rc = lib.stencil_mg_solve(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
+                              float(h), int(smoother), int(nu1), int(nu2), int(ncoarse), int(max_levels), float(rtol),
+                              int(max_cycles), ctypes.byref(rel), ctypes.byref(cyc), _stream(stream))
+    _check(ctx, rc, allow=(STENCIL_ERR_NOT_CONVERGED,))
+    return rel.value, cyc.value, rc == STENCIL_OK
 
 
 # ------------------------------------------------------------------ server --

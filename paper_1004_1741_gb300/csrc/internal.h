@@ -34,6 +34,8 @@ enum SlotId {
   SLOT_BATCH_TMP,        // batched Jacobi: second grids
   SLOT_TUNE_GRID,        // autotuner: copy of the caller's grid
   SLOT_GS_GOFF,          // Gauss-Seidel site offsets for one grid shape
+  SLOT_MG_LEVELS,        // multigrid: correction and right-hand side of every coarse level
+  SLOT_MG_R,             // multigrid: residual of the level being restricted
   SLOT_COUNT
 };
 
@@ -86,6 +88,8 @@ int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, 
 // `reduce`; returns status.  `result` receives the device pointer of the two sums.
 int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Geom& g, double h,
                     double* r_out, float* r32_out, double** result, cudaStream_t st);
+// copies the two sums of residual_launch to the host (blocking)
+int read_sums(stencil_ctx* ctx, const double* dres, double* sums, cudaStream_t st);
 // u[interior] += (double) e[interior]
 int correct_launch(stencil_ctx* ctx, double* u, const float* e, const Geom& g, cudaStream_t st);
 

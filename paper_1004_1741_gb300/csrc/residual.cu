@@ -143,7 +143,7 @@ int correct_launch(stencil_ctx* ctx, double* u, const float* e, const Geom& g, c
 }
 
 // Reads the two sums (||r||^2, ||f||^2) to the host.
-static int read_sums(stencil_ctx* ctx, const double* dres, double* sums, cudaStream_t st) {
+int read_sums(stencil_ctx* ctx, const double* dres, double* sums, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(sums, dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "reading residual sums");
