@@ -200,14 +200,14 @@ static int plan_build(stencil_ctx* ctx, DFPlan* pl, int kind, int n, const Geom*
 
 template <typename T>
 static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, int D, const SiteTable& tb,
-                        int int_adds) {
+                        int int_adds, bool any_f) {
   cudaStream_t gs = ctx->gstream;
   cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamBeginCapture");
   int rc = STENCIL_OK;
   e = cudaMemsetAsync(pl->dev + pl->b_desc + pl->b_task, 0, pl->b_flag + 256, gs);
   if (e == cudaSuccess && kind == DF_KIND_GS_COLUMN) {
-    rc = df_column_launch<T>(ctx, pl->run, W, H, int_adds, gs);
+    rc = df_column_launch<T>(ctx, pl->run, W, H, int_adds, any_f, gs);
   } else if (e == cudaSuccess) {
     rc = STENCIL_UNSUPPORTED_TILE;
 #define DF_TILE(WW, HH, DD)                                                                          \
@@ -261,7 +261,10 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
     if (e != cudaSuccess) return cuda_err(ctx, e, "cudaMallocHost(status word)");
   }
   // ---- find or build the plan of this shape
-  std::vector<long long> key = {(long long)sizeof(T), kind, n, W, H, D, nt, int_adds};
+  bool any_f = false;
+  for (int i = 0; f && i < n; ++i) any_f = any_f || f[i] != nullptr;
+  // the column-march kernel's shared memory holds an f ring only when some grid has f
+  std::vector<long long> key = {(long long)sizeof(T), kind, n, W, H, D, nt, int_adds, any_f ? 1 : 0};
   for (int i = 0; i < n; ++i) {
     key.push_back(geoms[i].nx);
     key.push_back(geoms[i].ny);
@@ -302,7 +305,7 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
   if (!pl->exec || pl->exec_timeout != timeout_ns || pl->exec_poison != poison || pl->exec_tb != tb.coords) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     pl->exec = nullptr;
-    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, tb, int_adds);
+    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, tb, int_adds, any_f);
     if (rc) return rc;
     pl->exec_timeout = timeout_ns;
     pl->exec_poison = poison;

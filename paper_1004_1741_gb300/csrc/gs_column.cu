@@ -39,13 +39,15 @@ __host__ __device__ constexpr int col_ring_slots(int tx) { return (tx + kColPF +
 // Row pitch: TX + 2 cells, 12 for TX = 8 (a warp then spans four rows whose
 // cells fall on distinct 8-byte banks).
 __host__ __device__ constexpr int col_row_pitch(int tx) { return tx == 8 ? 12 : tx + 2; }
+// Shared memory of one task: the ring of u (halo rows and columns included)
+// and, with a right-hand side, a ring of f (interior cells only, same slots).
 template <typename T, int TX, int TY>
-constexpr size_t col_smem_bytes() {
-  return (size_t)col_ring_slots(TX) * (TY + 2) * col_row_pitch(TX) * sizeof(T);
+constexpr size_t col_smem_bytes(bool has_f) {
+  return (size_t)col_ring_slots(TX) * ((TY + 2) * col_row_pitch(TX) + (has_f ? TX * TY : 0)) * sizeof(T);
 }
 
 // The task (I, J, K, p): sweep p of tile (I, J, K) in place on u; all threads
-// of the CTA (TX x TY) take part; ring: col_smem_bytes of shared memory.
+// of the CTA (TX x TY) take part; ring: col_smem_bytes(HAS_F) of shared memory.
 // Returns after a barrier, with all of the task's global writes issued.
 template <typename T, class Ar, bool HAS_F, int TX, int TY>
 __device__ __forceinline__ void gs_column_body(T* u, const T* __restrict__ f, const Geom& g, const Coef<T>& c,
@@ -55,7 +57,7 @@ __device__ __forceinline__ void gs_column_body(T* u, const T* __restrict__ f, co
   constexpr int R = col_ring_slots(TX);
   constexpr int RW = col_row_pitch(TX), RH = TY + 2;
   constexpr int PL = RW * RH;  // cells per slot
-  constexpr int FQ = 4;        // right-hand side: register queue depth
+  constexpr int FPL = TX * TY;  // cells per slot of the f ring
   const int i = threadIdx.x, j = threadIdx.y;
   const int x0 = I * TX, y0 = J * TY;
   const int x = x0 + i, y = y0 + j;
@@ -82,12 +84,14 @@ __device__ __forceinline__ void gs_column_body(T* u, const T* __restrict__ f, co
   const int hi_y = lo_y + nzl - 1;
   const int lo_c = i + j, hi_c = i + j + nzl - 1;        // update
   const int lo_w = TX + j + 1, hi_w = TX + j + nzl;      // write-back, planes 0..nzl-1
+  const int lo_f = j - 2 - PF, hi_f = j - 3 - PF + nzl;  // own row of f, planes 0..nzl-1
   auto inwin = [](int t, int lo, int hi) { return (unsigned)(t - lo) <= (unsigned)(hi - lo); };
   auto mod = [](int q) { return ((q % R) + R) % R; };
   // per-thread ring cells (slot 0) and the running slots of copies, update and write-back
   T* const cell = ring + (j + 1) * RW + (i + 1);
   T* const xcell = ring + (j + 1) * RW + (i == 0 ? 0 : TX + 1);
   T* const ycell = ring + (j == 0 ? 0 : TY + 1) * RW + (i + 1);
+  T* const fcell = ring + R * PL + j * TX + i;  // f ring: cell (i, j, k) in slot (k+i+j) mod R, like u
   const int xoff = i == 0 ? 1 + PF : 2 + PF + TX;  // column slot - t
   int sl = mod(ts + 2 + PF + i), sx = mod(ts + xoff), sw = mod(ts - TX - 1 + i), st = mod(ts);
   // global pointers at the plane of step ts
@@ -96,36 +100,26 @@ __device__ __forceinline__ void gs_column_body(T* u, const T* __restrict__ f, co
   const T* gy = u + (ldy ? g.at(x, j == 0 ? y0 - 1 : y0 + TY, z0) : 0) +
                 (int64_t)(j == 0 ? ts + 3 + PF : ts - TY + 2 + PF) * sy;
   T* gw = u + (comp ? g.at(x, y, z0) : 0) + (int64_t)(ts - TX - j - 1) * sy;
-  // right-hand side of planes kk .. kk+FQ-1, kk = t - i - j
-  const T* gf = HAS_F ? f + (comp ? g.at(x, y, z0) : 0) + (int64_t)(ts - i - j + FQ) * sy : nullptr;
-  T F[FQ];
-#pragma unroll
-  for (int m = 0; m < FQ; ++m) {
-    const int q = ts - i - j + m;
-    F[m] = (HAS_F && comp && q >= 0 && q < nzl) ? f[g.at(x, y, z0 + q)] : T(0);
-  }
+  // f: copied with the own row (plane t - j + 2 + PF, same slot), read at the update
+  const T* gf = HAS_F ? f + (comp ? g.at(x, y, z0) : 0) + (int64_t)(ts - j + 2 + PF) * sy : nullptr;
   auto wrap = [](int s) { return s == R - 1 ? 0 : s + 1; };
   for (int t = ts; t <= te; ++t) {
     const bool wl = inwin(t, lo_l, hi_l);
     if (ldo && wl) cp_async_elem(cell + sl * PL, go);
     if (ldx && wl) cp_async_elem(xcell + sx * PL, gx);
     if (ldy && inwin(t, lo_y, hi_y)) cp_async_elem(ycell + sl * PL, gy);
+    if (HAS_F && comp && inwin(t, lo_f, hi_f)) cp_async_elem(fcell + sl * FPL, gf);
     cp_async_commit();
     if (comp && inwin(t, lo_c, hi_c)) {
       const int sm1 = st == 0 ? R - 1 : st - 1, sp1 = wrap(st);
       const T* pm = cell + sm1 * PL;
       const T* pp = cell + sp1 * PL;
-      const T v = site_update<T, Ar, HAS_F, false>(pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], F[0], T(0), c);
+      const T fv = HAS_F ? fcell[st * FPL] : T(0);
+      const T v = site_update<T, Ar, HAS_F, false>(pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv, T(0), c);
       cell[st * PL] = v;
     }
     if (comp && inwin(t, lo_w, hi_w)) *gw = cell[sw * PL];
-    if (HAS_F) {
-#pragma unroll
-      for (int m = 0; m + 1 < FQ; ++m) F[m] = F[m + 1];
-      const int q = t - i - j + FQ;
-      F[FQ - 1] = (comp && q >= 0 && q < nzl) ? *gf : T(0);
-      gf += sy;
-    }
+    if (HAS_F) gf += sy;
     cp_async_wait<PF>();
     __syncthreads();
     sl = wrap(sl); sx = wrap(sx); sw = wrap(sw); st = wrap(st);
@@ -201,7 +195,7 @@ static int gs_column_levels(stencil_ctx* ctx, T* u, const T* f, const Geom& g, C
   const uint64_t* slices = slices_ptr(ctx);
   const int* soff = slice_off_ptr(ctx);
   auto kern = gs_column_kernel<T, Ar, HAS_F, TX, TY>;
-  const size_t smem = col_smem_bytes<T, TX, TY>();
+  const size_t smem = col_smem_bytes<T, TX, TY>(HAS_F);
   cudaError_t e0 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e0 != cudaSuccess) return cuda_err(ctx, e0, "gs_column_kernel shared memory");
   for (int L = 0; L < tg.nlevels; ++L) {
@@ -216,9 +210,9 @@ static int gs_column_levels(stencil_ctx* ctx, T* u, const T* f, const Geom& g, C
 }
 
 template <typename T, class Ar, int TX, int TY>
-static int df_column_launch_t(stencil_ctx* ctx, const DFRun& run, cudaStream_t st) {
+static int df_column_launch_t(stencil_ctx* ctx, const DFRun& run, bool any_f, cudaStream_t st) {
   auto kern = dataflow_column_kernel<T, Ar, TX, TY>;
-  const size_t smem = col_smem_bytes<T, TX, TY>();
+  const size_t smem = col_smem_bytes<T, TX, TY>(any_f);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_err(ctx, e, "dataflow_column_kernel shared memory");
   int per_sm = 0;
@@ -234,27 +228,27 @@ static int df_column_launch_t(stencil_ctx* ctx, const DFRun& run, cudaStream_t s
 }
 
 template <typename T, class Ar>
-static int df_column_tile(stencil_ctx* ctx, const DFRun& run, int tx, int ty, cudaStream_t st) {
-  if (tx == 8 && ty == 8) return df_column_launch_t<T, Ar, 8, 8>(ctx, run, st);
-  if (tx == 8 && ty == 16) return df_column_launch_t<T, Ar, 8, 16>(ctx, run, st);
-  if (tx == 16 && ty == 8) return df_column_launch_t<T, Ar, 16, 8>(ctx, run, st);
+static int df_column_tile(stencil_ctx* ctx, const DFRun& run, int tx, int ty, bool any_f, cudaStream_t st) {
+  if (tx == 8 && ty == 8) return df_column_launch_t<T, Ar, 8, 8>(ctx, run, any_f, st);
+  if (tx == 8 && ty == 16) return df_column_launch_t<T, Ar, 8, 16>(ctx, run, any_f, st);
+  if (tx == 16 && ty == 8) return df_column_launch_t<T, Ar, 16, 8>(ctx, run, any_f, st);
   return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column-march Gauss-Seidel tile %dx%d (supported 8x8, 8x16, 16x8)",
                  tx, ty);
 }
 
 template <typename T>
-int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, cudaStream_t st) {
+int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, cudaStream_t st) {
   if constexpr (sizeof(T) == 8) {
-    if (int_adds == 1) return df_column_tile<T, ArithF64Mix<0x1Du>>(ctx, run, tx, ty, st);
-    if (int_adds == 2) return df_column_tile<T, ArithF64Mix<0x15u>>(ctx, run, tx, ty, st);
-    if (int_adds == 3) return df_column_tile<T, ArithF64Mix<0x12u>>(ctx, run, tx, ty, st);
-    if (int_adds == 4) return df_column_tile<T, ArithF64Mix<0x10u>>(ctx, run, tx, ty, st);
-    if (int_adds == 5) return df_column_tile<T, ArithF64Mix<0x00u>>(ctx, run, tx, ty, st);
+    if (int_adds == 1) return df_column_tile<T, ArithF64Mix<0x1Du>>(ctx, run, tx, ty, any_f, st);
+    if (int_adds == 2) return df_column_tile<T, ArithF64Mix<0x15u>>(ctx, run, tx, ty, any_f, st);
+    if (int_adds == 3) return df_column_tile<T, ArithF64Mix<0x12u>>(ctx, run, tx, ty, any_f, st);
+    if (int_adds == 4) return df_column_tile<T, ArithF64Mix<0x10u>>(ctx, run, tx, ty, any_f, st);
+    if (int_adds == 5) return df_column_tile<T, ArithF64Mix<0x00u>>(ctx, run, tx, ty, any_f, st);
   }
-  return df_column_tile<T, typename DefaultArith<T>::type>(ctx, run, tx, ty, st);
+  return df_column_tile<T, typename DefaultArith<T>::type>(ctx, run, tx, ty, any_f, st);
 }
-template int df_column_launch<double>(stencil_ctx*, const DFRun&, int, int, int, cudaStream_t);
-template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, cudaStream_t);
+template int df_column_launch<double>(stencil_ctx*, const DFRun&, int, int, int, bool, cudaStream_t);
+template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, bool, cudaStream_t);
 
 // Column-march Gauss-Seidel: tiles tx x ty columns (8x8, 8x16, 16x8; default 8x8 for FP64, whose FP64
 // pipe favours the short ramp of narrow tiles, 16x8 for FP32) x tz planes (default: equal chunks of at

@@ -115,6 +115,6 @@ constexpr int DF_KIND_GS_COLUMN = 16;
 struct DFRun;
 // launch of the persistent column-march kernel for one dataflow run (gs_column.cu)
 template <typename T>
-int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, cudaStream_t st);
+int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, cudaStream_t st);
 
 }  // namespace stn
