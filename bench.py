@@ -476,6 +476,17 @@ def run_case(args):
     from paper_1004_1741_gb300 import capi, workloads
 
     ctx = capi.Context(0)
+    if args.case == "mg":  # --sweeps V-cycles of the multigrid solve on the sine-mode problem (FP64)
+        prob = workloads.sine_modes_problem(args.n, seed=4)
+        f = torch.from_numpy(prob.f).to("cuda")
+        u = torch.zeros_like(f)
+        sm = capi.STENCIL_GS if args.variant == 0 else capi.STENCIL_JACOBI
+        for _ in range(args.repeat):
+            capi.stencil_mg_solve(ctx, u, f, prob.h, sm, rtol=0.0, max_cycles=args.sweeps)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "mg", "n": args.n, "cycles": args.sweeps, "launches": ctx.kernel_launches}))
+        ctx.close()
+        return 0
     u = torch.from_numpy(workloads.laplace_cube(args.n)).to("cuda")
     dt = torch.float32 if args.dtype == "f32" else torch.float64
     u = u.to(dt)
@@ -668,7 +679,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
-    ap.add_argument("--case", choices=["jacobi", "gs"], help="run one smoother only (profiling case)")
+    ap.add_argument("--case", choices=["jacobi", "gs", "mg"],
+                    help="run one smoother (or the multigrid solve: --variant 0 GS, 1 Jacobi) only (profiling case)")
     ap.add_argument("--n", type=int, default=320)
     ap.add_argument("--sweeps", type=int, default=8)
     ap.add_argument("--nt", type=int, default=1)

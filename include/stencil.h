@@ -111,8 +111,8 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          5 = the column march as one persistent dataflow launch over the
  *          tasks (blocking, like 3; no launch boundary between levels);
  *          Gauss-Seidel default: variant 4 at nt = 1 without a tile (8x8
- *          for FP64, 16x8 for FP32, chunks of at most 100 planes),
- *          variant 2 otherwise;
+ *          for FP64, 16x8 for FP32, chunks of at most 100 planes, 16 for
+ *          calls of fewer than 8 sweeps), variant 2 otherwise;
  *          3 (both smoothers) = one persistent
  *          dataflow launch over a dependency-ordered task queue (blocking);
  *          Jacobi 1 = z-march, 2 = z-march with asynchronous plane copies,

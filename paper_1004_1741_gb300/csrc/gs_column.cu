@@ -252,15 +252,18 @@ template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, 
 
 // Column-march Gauss-Seidel: tiles tx x ty columns (8x8, 8x16, 16x8; default 8x8 for FP64, whose FP64
 // pipe favours the short ramp of narrow tiles, 16x8 for FP32) x tz planes (default: equal chunks of at
-// most 100 planes, enough tasks per level to fill the GPU while the march's ramp of tx + ty steps stays
-// short against the chunk).  persistent: one dataflow launch (blocking) instead of one launch per level.
+// most 100 planes -- 16 when the call runs fewer than 8 sweeps --, enough tasks per level to fill the
+// GPU while the march's ramp of tx + ty steps stays short against the chunk).  persistent: one dataflow launch (blocking) instead of one launch per level.
 template <typename T, class Ar>
 int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,
                   int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st) {
   if (tx == 0) tx = sizeof(T) == 8 ? 8 : 16;
   if (ty == 0) ty = 8;
   if (tz <= 0) {
-    const int chunks = (g.nz + 99) / 100;
+    // a call of few sweeps is bound by the fill and drain of the task wavefront (levels x task length):
+    // short chunks shorten it; many sweeps keep the GPU full and favour long chunks (short ramp per plane)
+    const int cap = nsweeps < 8 ? 16 : 100;
+    const int chunks = (g.nz + cap - 1) / cap;
     tz = (g.nz + chunks - 1) / chunks;
   }
   if (persistent) {

@@ -84,10 +84,11 @@ int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, 
                   int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st);
 
 // Residual r = f - A u; optional FP64 r and/or FP32 r32 on the interior;
-// sums of r^2 and f^2 into the context's result slot (device) when
-// `reduce`; returns status.  `result` receives the device pointer of the two sums.
+// sums of r^2 and f^2 into the context's result slot (device) when `norm`
+// (else FP64 r only, no sums); returns status.  `result` receives the device
+// pointer of the two sums.
 int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Geom& g, double h,
-                    double* r_out, float* r32_out, double** result, cudaStream_t st);
+                    double* r_out, float* r32_out, double** result, cudaStream_t st, bool norm = true);
 // copies the two sums of residual_launch to the host (blocking)
 int read_sums(stencil_ctx* ctx, const double* dres, double* sums, cudaStream_t st);
 // u[interior] += (double) e[interior]

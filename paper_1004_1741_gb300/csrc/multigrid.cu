@@ -109,7 +109,7 @@ int mg_vcycle(MGRun& m, int l) {
   int rc = mg_smooth(m, l, m.nu1);
   if (rc) return rc;
   double* dres;
-  if ((rc = residual_launch(m.ctx, L.u, L.f, L.g, L.h, m.r, nullptr, &dres, m.st))) return rc;
+  if ((rc = residual_launch(m.ctx, L.u, L.f, L.g, L.h, m.r, nullptr, &dres, m.st, false))) return rc;
   mg_restrict_kernel<<<dim3((C.g.nx + 31) / 32, (C.g.ny + 3) / 4, C.g.nz), dim3(32, 4), 0, m.st>>>(m.r, L.g, C.fw,
                                                                                                    C.g);
   m.ctx->launches++;

@@ -14,12 +14,14 @@ namespace stn {
 
 constexpr int RES_BX = 32, RES_BY = 8, RES_ZCHUNK = 32;
 
-template <bool HAS_F, bool WANT_R, bool WANT_R32>
+// NORM: also the per-CTA partial sums of r^2 and f^2.  The neighbour sum takes
+// three of its five additions on the integer pipes (common.cuh; same bits).
+template <bool HAS_F, bool WANT_R, bool WANT_R32, bool NORM>
 __global__ void __launch_bounds__(RES_BX* RES_BY) residual_kernel(const double* __restrict__ u,
                                                                   const double* __restrict__ f, double* r_out,
                                                                   float* r32_out, Geom g, double ih2,
                                                                   double* __restrict__ partials) {
-  using Ar = ArithF64;
+  using Ar = ArithF64Mix<0x12u>;
   const int x = blockIdx.x * RES_BX + threadIdx.x;
   const int y = blockIdx.y * RES_BY + threadIdx.y;
   const int z0 = blockIdx.z * RES_ZCHUNK;
@@ -28,20 +30,23 @@ __global__ void __launch_bounds__(RES_BX* RES_BY) residual_kernel(const double* 
   if (x < g.nx && y < g.ny) {
     for (int z = z0; z < z1; ++z) {
       const int64_t c = g.at(x, y, z);
-      double s = Ar::add(u[c - 1], u[c + 1]);
-      s = Ar::add(s, u[c - g.sx]);
-      s = Ar::add(s, u[c + g.sx]);
-      s = Ar::add(s, u[c - g.sy]);
-      s = Ar::add(s, u[c + g.sy]);
+      double s = Ar::template add_k<0>(u[c - 1], u[c + 1]);
+      s = Ar::template add_k<1>(s, u[c - g.sx]);
+      s = Ar::template add_k<2>(s, u[c + g.sx]);
+      s = Ar::template add_k<3>(s, u[c - g.sy]);
+      s = Ar::template add_k<4>(s, u[c + g.sy]);
       const double au = __dmul_rn(__dsub_rn(__dmul_rn(6.0, u[c]), s), ih2);
       const double fv = HAS_F ? f[c] : 0.0;
       const double r = __dsub_rn(fv, au);
       if (WANT_R) r_out[c] = r;
       if (WANT_R32) r32_out[c] = __double2float_rn(r);
-      rr = __fma_rn(r, r, rr);
-      if (HAS_F) ff = __fma_rn(fv, fv, ff);
+      if (NORM) {
+        rr = __fma_rn(r, r, rr);
+        if (HAS_F) ff = __fma_rn(fv, fv, ff);
+      }
     }
   }
+  if (!NORM) return;
   // fixed-order block reduction: warp tree, then warp 0 over the warp sums
   __shared__ double wr[RES_BY], wf[RES_BY];
   for (int o = 16; o > 0; o >>= 1) {
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(1024) reduce_pairs_kernel(const double* __rest
 }
 
 int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Geom& g, double h, double* r_out,
-                    float* r32_out, double** result, cudaStream_t st) {
+                    float* r32_out, double** result, cudaStream_t st, bool norm) {
   dim3 block(RES_BX, RES_BY);
   dim3 grid((g.nx + RES_BX - 1) / RES_BX, (g.ny + RES_BY - 1) / RES_BY, (g.nz + RES_ZCHUNK - 1) / RES_ZCHUNK);
   const int64_t nblk = (int64_t)grid.x * grid.y * grid.z;
@@ -102,8 +107,21 @@ int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Ge
   if (!res) return status;
   *result = res;
   const double ih2 = 1.0 / (h * h);
+  if (!norm) {  // r only (the multigrid cycle): no sums, no reduction
+    if (nblk > 0) {
+      if (!r_out || r32_out) return set_err(ctx, STENCIL_ERR_ARG, "residual without norm writes FP64 r only");
+      if (f)
+        residual_kernel<true, true, false, false><<<grid, block, 0, st>>>(u, f, r_out, nullptr, g, ih2, part);
+      else
+        residual_kernel<false, true, false, false><<<grid, block, 0, st>>>(u, f, r_out, nullptr, g, ih2, part);
+      ctx->launches++;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(ctx, e, "residual kernel");
+    return STENCIL_OK;
+  }
   if (nblk > 0) {
-#define RES_GO(HF, WR, W32) residual_kernel<HF, WR, W32><<<grid, block, 0, st>>>(u, f, r_out, r32_out, g, ih2, part)
+#define RES_GO(HF, WR, W32) residual_kernel<HF, WR, W32, true><<<grid, block, 0, st>>>(u, f, r_out, r32_out, g, ih2, part)
     const bool hf = f != nullptr, wr = r_out != nullptr, w32 = r32_out != nullptr;
     if (hf && wr && w32) RES_GO(true, true, true);
     else if (hf && wr) RES_GO(true, true, false);
