@@ -36,6 +36,7 @@ enum SlotId {
   SLOT_GS_GOFF,          // Gauss-Seidel site offsets for one grid shape
   SLOT_MG_LEVELS,        // multigrid: correction and right-hand side of every coarse level
   SLOT_MG_R,             // multigrid: residual of the level being restricted
+  SLOT_JACOBI_SLABS,     // in-place Jacobi: ring of two z-slabs of new values
   SLOT_COUNT
 };
 

@@ -11,7 +11,11 @@
 // of a site update per lattice update and nothing else.
 //
 // Temporal blocking (nt > 1 sweeps per pass) is implemented by the
-// skewed-tile task scheduler in tb_tasks.cu.
+// skewed-tile task scheduler in tb_jacobi.cu and, for FP32, on chip in
+// tb_zmarch.cu; the in-place form without a second grid (variant 6) runs the
+// same z-march slab by slab.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace stn {
@@ -248,10 +252,75 @@ static Coef<T> make_coef(double h, const stencil_params* p) {
   return c;
 }
 
+// In-place Jacobi with a ring of two slabs (the paper's in-place temp-ring Jacobi, Sec. 4, restated for a
+// GPU): the grid is cut into z-slabs of S planes; slab s's new planes are computed from u into ring buffer
+// s % 2 (the z-march on a sub-geometry whose pointers start at the slab), and only then is slab s-1's
+// buffer copied back into u.  Slab s reads u's planes k0-1 .. k1, all still old: slab s-1 is written back
+// after slab s is computed, slab s+1 later still.  No second grid: the workspace is 2 S planes.
+template <typename T>
+__global__ void __launch_bounds__(256) slab_copy_back_kernel(T* __restrict__ u, const T* __restrict__ slab, Geom g,
+                                                             int k0, int planes) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int64_t o = (int64_t)(y + 1) * g.sx + (x + 1);
+  for (int z = blockIdx.z; z < planes; z += gridDim.z) u[g.at(x, y, k0 + z)] = slab[(int64_t)z * g.sy + o];
+}
+
+template <typename T>
+static int jacobi_inplace_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
+                              const stencil_params* p, cudaStream_t st) {
+  const int nt = (p && p->nt > 0) ? p->nt : 1;
+  if (nt != 1) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "in-place Jacobi runs nt = 1 only");
+  const int S = std::min((p && p->tile_z > 0) ? p->tile_z : 32, g.nz);
+  int by = (p && p->tile_y) ? p->tile_y : (sizeof(T) == 8 ? 4 : 8);
+  if (by != 4 && by != 8 && by != 16)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Jacobi tile_y = %d (supported 4, 8, 16)", by);
+  if (p && p->tile_x && p->tile_x != 32)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Jacobi tile_x = %d (supported 32)", p->tile_x);
+  const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsJacobi;
+  if (int_adds < 0 || int_adds > 5)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
+  int status = STENCIL_OK;
+  T* ring = (T*)ws_get(ctx, SLOT_JACOBI_SLABS, 2 * (size_t)S * (size_t)g.sy * sizeof(T), &status);
+  if (!ring) return status;
+  const Coef<T> c = make_coef<T>(h, p);
+  const bool weighted = p && p->a != 0.0;
+  const int nslab = (g.nz + S - 1) / S;
+  const dim3 cgrid((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)std::min(S, 64));
+  for (int sw = 0; sw < nsweeps; ++sw) {
+    for (int s = 0; s <= nslab; ++s) {
+      if (s < nslab) {
+        const int k0 = s * S, planes = std::min(S, g.nz - k0);
+        Geom gs = g;
+        gs.nz = planes;
+        T* buf = ring + (size_t)(s % 2) * S * g.sy;
+        // gs.at(x, y, z) = (z+1)*sy + ...: u and f from plane k0, the buffer from its first plane
+        const int64_t off = (int64_t)k0 * g.sy;
+        const int zchunk = std::max(16, planes);
+        cudaError_t e = jacobi_sweep<T>(u + off, buf - g.sy, f ? f + off : nullptr, gs, by, zchunk, c, weighted,
+                                        false, int_adds, st);
+        ctx->launches++;
+        if (e != cudaSuccess) return cuda_err(ctx, e, "jacobi_zmarch_kernel launch (slab)");
+      }
+      if (s > 0) {
+        const int k0 = (s - 1) * S, planes = std::min(S, g.nz - k0);
+        slab_copy_back_kernel<T><<<cgrid, dim3(32, 8), 0, st>>>(u, ring + (size_t)((s - 1) % 2) * S * g.sy, g, k0,
+                                                                planes);
+        ctx->launches++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_err(ctx, e, "slab copy-back");
+      }
+    }
+  }
+  return STENCIL_OK;
+}
+
 template <typename T>
 int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps, const stencil_params* p,
                cudaStream_t st) {
   if (nsweeps == 0 || g.nx == 0 || g.ny == 0 || g.nz == 0) return STENCIL_OK;
+  if (p && p->variant == 6) return jacobi_inplace_run<T>(ctx, u, f, g, h, nsweeps, p, st);
   const size_t bytes = (size_t)g.sy * (size_t)(g.nz + 2) * sizeof(T);
   int status = STENCIL_OK;
   T* tmp = (T*)ws_get(ctx, SLOT_JACOBI_TMP, bytes, &status);

@@ -407,3 +407,32 @@ def test_full_size_400_bench_config(ctx, smoother):
         got = _run(ctx, fn, u0, None, 1.0, 100, nt=cfg["nt"], tile=cfg["tile"], variant=cfg["variant"])
         ref = fut.result()
     _assert_exact(got, ref, "400^3 %s" % smoother)
+
+
+# ------------------------------------------------------------ in-place Jacobi --
+@pytest.mark.parametrize("dims", RAGGED + [(45, 38, 29), (33, 9, 70)])
+@pytest.mark.parametrize("slab", [0, 1, 2, 7, 32, 1000])
+def test_jacobi_inplace_slab_ring(ctx, dims, slab):
+    """variant 6: no second grid; z-slabs of `slab` planes into a ring of two buffers,
+    copied back one slab behind: bit-exact for odd and even sweep counts, with f,
+    weighted, FP32."""
+    u0, f0 = W.random_grid(*dims, seed=13, with_f=True)
+    for ns, ff, a, b in ((1, f0, 0.0, 0.0), (4, None, 0.0, 0.0), (3, f0, 0.25, 0.125)):
+        _assert_exact(_run(ctx, capi.stencil_jacobi, u0, ff, 0.07, ns, tile=(0, 0, slab), variant=6, a=a, b=b),
+                      oracle.jacobi(u0, ff, 0.07, ns, a=a, b=(b or None)), "inplace %s slab=%d ns=%d" % (dims, slab, ns))
+    u1, f1 = W.random_grid(*dims, seed=14, dtype=np.float32, with_f=True)
+    _assert_exact(_run(ctx, capi.stencil_jacobi, u1, f1, 0.07, 5, tile=(0, 0, slab), variant=6),
+                  oracle.jacobi(u1, f1, 0.07, 5), "inplace f32 %s slab=%d" % (dims, slab))
+
+
+def test_jacobi_inplace_needs_no_second_grid():
+    """The in-place form's workspace is two slabs, not a grid."""
+    c = capi.Context(0)
+    n = 128
+    u0, _ = W.random_grid(n, n, n, seed=1)
+    _run(c, capi.stencil_jacobi, u0, None, 1.0, 3, tile=(0, 0, 16), variant=6)
+    grid_bytes = u0.nbytes
+    assert c.workspace_bytes < grid_bytes / 2
+    with pytest.raises(capi.StencilError):
+        capi.stencil_jacobi(c, _dev(u0), None, 1.0, 2, nt=2, variant=6)
+    c.close()
