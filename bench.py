@@ -469,8 +469,10 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
 
 
 def run_case(args):
-    """One smoother on an n^3 FP64 grid (halo seed 1, interior seed 2), --repeat calls
-    of --sweeps sweeps: the small case for profiler captures."""
+    """One smoother on an n^3 grid (halo seed 1, interior seed 2; --poisson adds f ~ N(0,1)),
+    --repeat calls of --sweeps sweeps, timed with CUDA events: the small case for profiler
+    captures and single-configuration timings."""
+    import numpy as np
     import torch
 
     from paper_1004_1741_gb300 import capi, workloads
@@ -490,13 +492,27 @@ def run_case(args):
     u = torch.from_numpy(workloads.laplace_cube(args.n)).to("cuda")
     dt = torch.float32 if args.dtype == "f32" else torch.float64
     u = u.to(dt)
+    f = None
+    if args.poisson:  # f ~ N(0,1) on the interior (seed 1), h = 1/(n+1)
+        rng = np.random.default_rng(1)
+        fh = np.zeros(u.shape)
+        fh[1:-1, 1:-1, 1:-1] = rng.standard_normal((args.n,) * 3)
+        f = torch.from_numpy(fh).to("cuda").to(dt)
+    h = 1.0 / (args.n + 1) if args.poisson else 1.0
     fn = capi.stencil_jacobi if args.case == "jacobi" else capi.stencil_gs_lex
     tile = tuple(int(x) for x in args.tile.split(",")) if args.tile else (0, 0, 0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
     for _ in range(args.repeat):
-        fn(ctx, u, None, 1.0, args.sweeps, nt=args.nt, tile=tile, variant=args.variant, int_adds=args.int_adds)
+        fn(ctx, u, f, h, args.sweeps, nt=args.nt, tile=tile, variant=args.variant, int_adds=args.int_adds)
+    b.record()
     torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
     print(json.dumps({"case": args.case, "n": args.n, "sweeps": args.sweeps, "nt": args.nt, "repeat": args.repeat,
-                      "variant": args.variant, "int_adds": args.int_adds, "launches": ctx.kernel_launches}))
+                      "variant": args.variant, "int_adds": args.int_adds, "dtype": args.dtype,
+                      "poisson": bool(args.poisson), "launches": ctx.kernel_launches, "ms": ms,
+                      "glups": args.n ** 3 * args.sweeps * args.repeat / ms / 1e6,
+                      "workspace_mb": ctx.workspace_bytes / 1e6}))
     ctx.close()
     return 0
 
@@ -688,6 +704,7 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
     ap.add_argument("--variant", type=int, default=0, help="kernel variant of the profiling case")
     ap.add_argument("--int-adds", type=int, default=-1, help="integer-pipe additions of the profiling case")
+    ap.add_argument("--poisson", action="store_true", help="profiling case with f ~ N(0,1) instead of f = 0")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--suite", choices=["mixed", "served", "mg"], help="a secondary workload instead of the headline")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")
