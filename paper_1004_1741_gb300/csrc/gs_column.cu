@@ -33,12 +33,12 @@ namespace stn {
 constexpr int kColPF = 2;  // steps of copies in flight ahead of their first reader
 // Ring depth: a cell's slot is refilled only after its row has been written
 // back: a row line lives from its copy (PF+1 steps before its first reader)
-// to its write-back (TX+2 steps after), so R >= TX + PF + 4, rounded up to a
-// multiple of 4.
-__host__ __device__ constexpr int col_ring_slots(int tx) { return (tx + kColPF + 4 + 3) / 4 * 4; }
-// Row pitch: TX + 2 cells, 12 for TX = 8 (a warp then spans four rows whose
-// cells fall on distinct 8-byte banks).
-__host__ __device__ constexpr int col_row_pitch(int tx) { return tx == 8 ? 12 : tx + 2; }
+// to its write-back (TX+2 steps after), so R = TX + PF + 4 slots.
+__host__ __device__ constexpr int col_ring_slots(int tx) { return tx + kColPF + 4; }
+// Row pitch: the TX columns and their two neighbours.  (In 8-wide tiles a
+// half-warp's two rows then share some 8-byte banks; layouts that avoid it
+// measured slower or equal, and the smaller ring keeps more CTAs resident.)
+__host__ __device__ constexpr int col_row_pitch(int tx) { return tx + 2; }
 // Shared memory of one task: the ring of u (halo rows and columns included)
 // and, with a right-hand side, a ring of f (interior cells only, same slots).
 template <typename T, int TX, int TY>
