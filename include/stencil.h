@@ -312,9 +312,10 @@ void stencil_server_destroy(stencil_server* srv);
 
 /* Self-check of the integer-pipe binary64 addition: n pairs drawn from a
  * counter-based generator seeded by `seed` (random magnitudes, ties, carries,
- * zeros, signs), each summed on the integer pipes and on the FP64 pipe.
- * *out_mismatch (host) receives the number of pairs whose bits differ (must
- * be 0), *out_fast the number the integer path handled.  Blocking. */
+ * zeros, signs), each summed on the integer pipes (the symmetric form, and the
+ * ordered form in both argument orders) and on the FP64 pipe.  *out_mismatch
+ * (host) receives the number of integer-pipe sums whose bits differ (must be
+ * 0), *out_fast the number of pairs the symmetric form handled.  Blocking. */
 int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t seed, uint64_t* out_mismatch,
                              uint64_t* out_fast);
 

@@ -88,6 +88,32 @@ __device__ __forceinline__ bool int_add_f64(double a, double b, double* out) {
   return true;
 }
 
+// The same addition for an ordered pair: the fast path needs the exponent of a
+// at least that of b (and at most 10 above it), so no swap is needed; every
+// other pair, including a with the smaller exponent, goes to the FP64 pipe.
+// In the neighbour sum every addition after the first adds one neighbour to a
+// running sum of two to five positive values, which almost always satisfies it.
+__device__ __forceinline__ bool int_add_f64_ge(double a, double b, double* out) {
+  const unsigned hhi = (unsigned)__double2hiint(a), hlo = (unsigned)__double2loint(a);
+  const unsigned lhi = (unsigned)__double2hiint(b), llo = (unsigned)__double2loint(b);
+  const unsigned eh = hhi >> 20;  // sign bit included: negatives fail below
+  const unsigned d = eh - (lhi >> 20);
+  if (!((eh - 11u) < 2035u && d <= 10u)) return false;  // also fails when b's exponent is larger (d wraps)
+  const unsigned mh = (hhi & 0xFFFFFu) | 0x100000u, ml = (lhi & 0xFFFFFu) | 0x100000u;
+  const unsigned sh = 10u - d;
+  const unsigned long long MH = ((unsigned long long)__funnelshift_l(hlo, mh, 10) << 32) | (hlo << 10);
+  const unsigned long long ML = ((unsigned long long)__funnelshift_l(llo, ml, sh) << 32) | (llo << sh);
+  const unsigned long long S = MH + ML;
+  const unsigned shi = (unsigned)(S >> 32), slo = (unsigned)S;
+  const unsigned c = shi >> 31;
+  const unsigned s2lo = __funnelshift_r(slo, shi, c) | (slo & c), s2hi = shi >> c;
+  const unsigned long long R = (((unsigned long long)s2hi << 32) | s2lo) + (0x1FFu + ((s2lo >> 10) & 1u));
+  const unsigned rlo = (unsigned)R, rhi = (unsigned)(R >> 32);
+  const unsigned mlo = __funnelshift_r(rlo, rhi, 10), mhi = (rhi >> 10) + ((eh + c - 1u) << 20);
+  *out = __hiloint2double((int)mhi, (int)mlo);
+  return true;
+}
+
 // FP64 arithmetic that splits the additions of a site update between the
 // integer pipes (int_add_f64) and the FP64 pipe: the additions whose bit is
 // set in NATIVE_MASK (0 = first, 4 = last of the neighbour sum) and every
@@ -100,7 +126,8 @@ struct ArithF64Mix {
   static __device__ __forceinline__ double add_k(double a, double b) {
     if (NATIVE_MASK & (1u << K)) return ArithF64Fma::add(a, b);
     double r;
-    if (int_add_f64(a, b, &r)) return r;
+    // the first addition (W + E) has no preferred order; later ones add a neighbour to the running sum
+    if (K == 0 ? int_add_f64(a, b, &r) : int_add_f64_ge(a, b, &r)) return r;
     return ArithF64Fma::add(a, b);
   }
 };

@@ -99,8 +99,8 @@ constexpr int STENCIL_UNSUPPORTED_TILE = 1;
 // default number of FP64 neighbour-sum additions done on the integer pipes,
 // the balance of the FP64 pipe against the (half-rate) integer ALU pipe
 // measured at 400^3, 100 sweeps: Jacobi z-march (32x4) 81 GLUP/s at 0, 121 at
-// 2, 138 at 3, 114 at 4, 96 at 5; Gauss-Seidel column march (8x8) 100.6 at 2,
-// 96.7 at 3, 83.6 at 4; Gauss-Seidel tile tasks 66 at 0, 71 at 1, 70.5 at 2
+// 2, 148 at 3, 129 at 4; Gauss-Seidel column march (8x8, persistent) 105 at 2,
+// 103 at 3; Gauss-Seidel tile tasks 66 at 0, 71 at 1, 70.5 at 2
 constexpr int kDefaultIntAdds = 1;
 constexpr int kDefaultIntAddsJacobi = 3;
 constexpr int kDefaultIntAddsColumn = 2;

@@ -1,5 +1,6 @@
-// Self-check of the integer-pipe binary64 addition (common.cuh int_add_f64)
-// against the FP64 pipe on generated operand pairs.
+// Self-check of the integer-pipe binary64 additions (common.cuh int_add_f64 and
+// its ordered form int_add_f64_ge) against the FP64 pipe on generated operand
+// pairs.
 #include "internal.h"
 
 namespace stn {
@@ -44,12 +45,15 @@ __global__ void selftest_int_add_kernel(unsigned long long n, unsigned long long
     double b = gen_operand(r1, r2 >> 7, kind2);
     if ((r3 >> 8) & 1ull) b = __longlong_as_double(__double_as_longlong(a) + (long long)((r3 >> 9) & 15ull) - 8);
     if (((r3 >> 13) & 15ull) == 0) b = 0.0;
+    const double ref = __dadd_rn(a, b);
     double em;
     if (int_add_f64(a, b, &em)) {
       ++fast;
-      const double ref = __dadd_rn(a, b);
       if (__double_as_longlong(em) != __double_as_longlong(ref)) ++mism;
     }
+    // the ordered form, in both argument orders
+    if (int_add_f64_ge(a, b, &em) && __double_as_longlong(em) != __double_as_longlong(ref)) ++mism;
+    if (int_add_f64_ge(b, a, &em) && __double_as_longlong(em) != __double_as_longlong(__dadd_rn(b, a))) ++mism;
   }
   atomicAdd(counts, mism);
   atomicAdd(counts + 1, fast);
