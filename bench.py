@@ -55,10 +55,11 @@ FP64_ALU_PEAK_TOPS = 152 * 2 * 2.070e9 / 1e12
 # per SM, ncu sm__inst_executed_pipe_alu.avg.peak_sustained = 2 warp instructions per
 # cycle), each costing INT_ADD_ALU_INSTR ALU warp instructions per warp of additions
 # (ncu: the Jacobi z-march executes 20.0 ALU warp instructions per warp of sites with
-# no integer additions and 117.4 with three).  With the multiply on the FP64 pipe and
-# the five additions split freely, the two pipes together retire at most
-# (2 + 64 / INT_ADD_ALU_INSTR) operations per clock per SM: the bound reported below.
-INT_ADD_ALU_INSTR = (117.4 - 20.0) / 3
+# no integer additions and 103.4 with three, one symmetric and two ordered).  With the
+# multiply on the FP64 pipe and the five additions split freely, the two pipes together
+# retire at most (2 + 64 / INT_ADD_ALU_INSTR) operations per clock per SM: the bound
+# reported below.
+INT_ADD_ALU_INSTR = (103.4 - 20.0) / 3
 FP64_COMBINED_PEAK_TOPS = 152 * (2 + 64 / INT_ADD_ALU_INSTR) * 2.070e9 / 1e12
 
 
