@@ -117,10 +117,10 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          dataflow launch over a dependency-ordered task queue (blocking);
  *          Jacobi 1 = z-march, 2 = z-march with asynchronous plane copies,
  *          4 = FP32 temporal blocking on chip (nt <= 4, tile_y 16 or 32),
- *          6 = in place without a second grid (nt = 1): z-slabs of
- *          tile_z planes (default 32) are computed into a ring of two slab
- *          buffers and copied back one slab behind (workspace 2 tile_z
- *          planes instead of a whole grid).
+ *          6 = in place without a second grid (nt = 1, tile_y 4 or 8):
+ *          z-slabs of tile_z planes (default 32) are computed into a ring
+ *          of three slab buffers and copied back two slabs behind
+ *          (workspace 3 tile_z planes instead of a whole grid).
  *          Jacobi default: FP32 unweighted sweeps with nt <= 4 run variant 4
  *          (at nt = 1 only when tile_y is 0); FP64, weighted and the rest
  *          run the z-march at nt = 1 and skewed tiles at nt > 1.
@@ -142,7 +142,7 @@ typedef struct stencil_params {
  * Applies nsweeps >= 0 sweeps to u in place: after the call u holds the
  * nsweeps-th Jacobi iterate (whatever the parity of nsweeps).  The second
  * array of the out-of-place sweep comes from the context's workspace
- * (one grid's size, or two slabs with variant 6; STENCIL_ERR_OOM beyond the
+ * (one grid's size, or three slabs with variant 6; STENCIL_ERR_OOM beyond the
  * budget).  f: device pointer of
  * the same padded shape, or NULL for f = 0.  h > 0 (used only when f != NULL).
  * params may be NULL. */

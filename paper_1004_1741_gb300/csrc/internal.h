@@ -79,6 +79,10 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
 template <typename T>
 int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
            const stencil_params* p, cudaStream_t st);
+// Jacobi in place without a second grid (jacobi_inplace.cu; stencil_params variant 6)
+template <typename T>
+int jacobi_inplace_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
+                       const stencil_params* p, cudaStream_t st);
 // column-march Gauss-Seidel, one sweep per task (gs_column.cu); zero tile extents: defaults
 template <typename T, class Ar>
 int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,

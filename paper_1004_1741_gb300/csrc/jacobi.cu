@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "zmarch.cuh"
 
 namespace stn {
 
@@ -25,64 +26,10 @@ __global__ void __launch_bounds__(32 * BY) jacobi_zmarch_kernel(const T* __restr
                                                                 const T* __restrict__ f, Geom g, int zchunk,
                                                                 Coef<T> c) {
   __shared__ T sm[2][BY + 2][32 + 2];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x = blockIdx.x * 32 + tx;
-  const int y = blockIdx.y * BY + ty;
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(g.nz, z0 + zchunk);
   if (z0 >= z1) return;  // uniform over the block
-  const bool inside = (x <= g.nx) && (y <= g.ny);  // own column lies in the interior or the +1 halo
-  const bool active = (x < g.nx) && (y < g.ny);    // own column is an interior column
-  // halo duties (each at most one extra column or row)
-  const bool hw = (tx == 0) && (y <= g.ny);                     // column x-1 (>= -1)
-  const bool he = (tx == 31) && (x + 1 <= g.nx) && (y <= g.ny);  // column x+1
-  const bool hs = (ty == 0) && (x <= g.nx);                     // row y-1 (>= -1)
-  const bool hn = (ty == BY - 1) && (y + 1 <= g.ny) && (x <= g.nx);
-  const int64_t sy = g.sy;
-  // pointers at plane z (advanced by one plane per step; dereferenced only when in range)
-  const int64_t o0 = (int64_t)(z0 + 1) * sy;
-  const T* pc = src + (inside ? g.at(x, y, -1) : 0) + o0;
-  const T* pw = src + (hw ? g.at(x - 1, y, -1) : 0) + o0;
-  const T* pe = src + (he ? g.at(x + 1, y, -1) : 0) + o0;
-  const T* ps = src + (hs ? g.at(x, y - 1, -1) : 0) + o0;
-  const T* pn = src + (hn ? g.at(x, y + 1, -1) : 0) + o0;
-  const int64_t od = (inside ? g.at(x, y, -1) : 0) + o0;
-  T* pd = dst + od;
-  const T* pf = HAS_F ? f + od : nullptr;
-  T below = inside ? pc[-sy] : T(0);
-  T cur = inside ? pc[0] : T(0);
-  T above = inside ? pc[sy] : T(0);
-  auto step = [&](int z, int bf) {
-    sm[bf][ty + 1][tx + 1] = cur;
-    if (hw) sm[bf][ty + 1][0] = *pw;
-    if (he) sm[bf][ty + 1][33] = *pe;
-    if (hs) sm[bf][0][tx + 1] = *ps;
-    if (hn) sm[bf][BY + 1][tx + 1] = *pn;
-    // prefetch plane z+2 (exists up to the top halo plane nz)
-    const T next = (inside && z + 2 <= g.nz) ? pc[2 * sy] : T(0);
-    T fv = T(0);
-    if (HAS_F && active) fv = *pf;
-    __syncthreads();
-    if (active)
-      *pd = site_update<T, Ar, HAS_F, WEIGHTED>(sm[bf][ty + 1][tx], sm[bf][ty + 1][tx + 2], sm[bf][ty][tx + 1],
-                                                sm[bf][ty + 2][tx + 1], below, above, fv, cur, c);
-    below = cur;
-    cur = above;
-    above = next;
-    pc += sy;
-    pw += sy;
-    pe += sy;
-    ps += sy;
-    pn += sy;
-    pd += sy;
-    if (HAS_F) pf += sy;
-  };
-  int z = z0;
-  for (; z + 1 < z1; z += 2) {  // two planes per trip: the buffer index is a constant
-    step(z, 0);
-    step(z + 1, 1);
-  }
-  if (z < z1) step(z, 0);
+  zmarch_body<T, Ar, HAS_F, WEIGHTED, BY>(src, dst, f, g, z0, z1, c, sm);
 }
 
 // Pipelined variant: the same 2.5D z-march, but planes arrive in shared
@@ -250,70 +197,6 @@ static Coef<T> make_coef(double h, const stencil_params* p) {
   c.b = (T)b;
   c.hh = (T)(h * h);
   return c;
-}
-
-// In-place Jacobi with a ring of two slabs (the paper's in-place temp-ring Jacobi, Sec. 4, restated for a
-// GPU): the grid is cut into z-slabs of S planes; slab s's new planes are computed from u into ring buffer
-// s % 2 (the z-march on a sub-geometry whose pointers start at the slab), and only then is slab s-1's
-// buffer copied back into u.  Slab s reads u's planes k0-1 .. k1, all still old: slab s-1 is written back
-// after slab s is computed, slab s+1 later still.  No second grid: the workspace is 2 S planes.
-template <typename T>
-__global__ void __launch_bounds__(256) slab_copy_back_kernel(T* __restrict__ u, const T* __restrict__ slab, Geom g,
-                                                             int k0, int planes) {
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * 8 + threadIdx.y;
-  if (x >= g.nx || y >= g.ny) return;
-  const int64_t o = (int64_t)(y + 1) * g.sx + (x + 1);
-  for (int z = blockIdx.z; z < planes; z += gridDim.z) u[g.at(x, y, k0 + z)] = slab[(int64_t)z * g.sy + o];
-}
-
-template <typename T>
-static int jacobi_inplace_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
-                              const stencil_params* p, cudaStream_t st) {
-  const int nt = (p && p->nt > 0) ? p->nt : 1;
-  if (nt != 1) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "in-place Jacobi runs nt = 1 only");
-  const int S = std::min((p && p->tile_z > 0) ? p->tile_z : 32, g.nz);
-  int by = (p && p->tile_y) ? p->tile_y : (sizeof(T) == 8 ? 4 : 8);
-  if (by != 4 && by != 8 && by != 16)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Jacobi tile_y = %d (supported 4, 8, 16)", by);
-  if (p && p->tile_x && p->tile_x != 32)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Jacobi tile_x = %d (supported 32)", p->tile_x);
-  const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsJacobi;
-  if (int_adds < 0 || int_adds > 5)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
-  int status = STENCIL_OK;
-  T* ring = (T*)ws_get(ctx, SLOT_JACOBI_SLABS, 2 * (size_t)S * (size_t)g.sy * sizeof(T), &status);
-  if (!ring) return status;
-  const Coef<T> c = make_coef<T>(h, p);
-  const bool weighted = p && p->a != 0.0;
-  const int nslab = (g.nz + S - 1) / S;
-  const dim3 cgrid((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)std::min(S, 64));
-  for (int sw = 0; sw < nsweeps; ++sw) {
-    for (int s = 0; s <= nslab; ++s) {
-      if (s < nslab) {
-        const int k0 = s * S, planes = std::min(S, g.nz - k0);
-        Geom gs = g;
-        gs.nz = planes;
-        T* buf = ring + (size_t)(s % 2) * S * g.sy;
-        // gs.at(x, y, z) = (z+1)*sy + ...: u and f from plane k0, the buffer from its first plane
-        const int64_t off = (int64_t)k0 * g.sy;
-        const int zchunk = std::max(16, planes);
-        cudaError_t e = jacobi_sweep<T>(u + off, buf - g.sy, f ? f + off : nullptr, gs, by, zchunk, c, weighted,
-                                        false, int_adds, st);
-        ctx->launches++;
-        if (e != cudaSuccess) return cuda_err(ctx, e, "jacobi_zmarch_kernel launch (slab)");
-      }
-      if (s > 0) {
-        const int k0 = (s - 1) * S, planes = std::min(S, g.nz - k0);
-        slab_copy_back_kernel<T><<<cgrid, dim3(32, 8), 0, st>>>(u, ring + (size_t)((s - 1) % 2) * S * g.sy, g, k0,
-                                                                planes);
-        ctx->launches++;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_err(ctx, e, "slab copy-back");
-      }
-    }
-  }
-  return STENCIL_OK;
 }
 
 template <typename T>

@@ -413,9 +413,9 @@ def test_full_size_400_bench_config(ctx, smoother):
 @pytest.mark.parametrize("dims", RAGGED + [(45, 38, 29), (33, 9, 70)])
 @pytest.mark.parametrize("slab", [0, 1, 2, 7, 32, 1000])
 def test_jacobi_inplace_slab_ring(ctx, dims, slab):
-    """variant 6: no second grid; z-slabs of `slab` planes into a ring of two buffers,
-    copied back one slab behind: bit-exact for odd and even sweep counts, with f,
-    weighted, FP32."""
+    """variant 6: no second grid; z-slabs of `slab` planes into a ring of three buffers,
+    copied back two slabs behind: bit-exact for odd and even sweep counts, with f,
+    weighted, FP32 (one, two and many slabs)."""
     u0, f0 = W.random_grid(*dims, seed=13, with_f=True)
     for ns, ff, a, b in ((1, f0, 0.0, 0.0), (4, None, 0.0, 0.0), (3, f0, 0.25, 0.125)):
         _assert_exact(_run(ctx, capi.stencil_jacobi, u0, ff, 0.07, ns, tile=(0, 0, slab), variant=6, a=a, b=b),
@@ -426,7 +426,7 @@ def test_jacobi_inplace_slab_ring(ctx, dims, slab):
 
 
 def test_jacobi_inplace_needs_no_second_grid():
-    """The in-place form's workspace is two slabs, not a grid."""
+    """The in-place form's workspace is three slabs, not a grid."""
     c = capi.Context(0)
     n = 128
     u0, _ = W.random_grid(n, n, n, seed=1)
