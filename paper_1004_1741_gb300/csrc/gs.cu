@@ -17,6 +17,10 @@
 // sites it updated.  nt sweeps per task is the paper's wavefront temporal
 // blocking: the tile stays on chip for nt sweeps and the grid is read and
 // written once per nt sweeps.
+//
+// With one sweep per pass and no explicit tile the column march of
+// gs_column.cu (variants 4 and 5) runs instead: the same nt = 1 task order,
+// a thread per column inside each task.
 #include <algorithm>
 #include <vector>
 
@@ -117,7 +121,8 @@ __global__ void __launch_bounds__(GS_THREADS) gs_task_kernel(T* __restrict__ u, 
   }
 }
 
-// Direct variant (default): the task body of task_bodies.cuh, one CTA per task
+// Direct variant (variant 2; the default for nt > 1 or an explicit tile): the
+// task body of task_bodies.cuh, one CTA per task
 // of the level.
 template <typename T, class Ar, bool HAS_F, int W, int H, int D>
 __global__ void __launch_bounds__(GS_THREADS) gs_direct_kernel(T* u, const T* __restrict__ f, Geom g, Coef<T> c,
