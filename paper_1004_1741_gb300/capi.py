@@ -286,7 +286,8 @@ def residual_norm(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: floa
 
 def stencil_batched(ctx: Context, us, fs, hs, nsweeps, smoother: int, *, nt: int = 0, tile=(0, 0, 0),
                     variant: int = 0, int_adds: int = -1, stream=None) -> None:
-    """Smooth many grids (a list of tensors, one dtype) in one persistent launch."""
+    """Smooth many grids (a list of tensors, one dtype): one persistent launch, or one z-march launch per sweep
+    for Jacobi at nt = 1."""
     lib = load_library()
     n = len(us)
     if n == 0:

@@ -41,6 +41,22 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
     return dataflow_run<T>(ctx, DF_KIND_GS_COLUMN, n, a.data(), nullptr, fs.data(), geoms.data(), nsweeps, h, cx, cy,
                            cz, 1, ctx->df_timeout_ns, ctx->df_poison, st, (double)(T)bco, ia);
   }
+  // Jacobi with one sweep per pass: one z-march launch per sweep over all grids unless a task variant is asked for
+  if (smoother == STENCIL_JACOBI && nt == 1 && (!p || p->variant == 0)) {
+    if (p && p->a != 0.0) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "weighted sweeps are not batched");
+    std::vector<T*> uu((size_t)n);
+    std::vector<const T*> ff((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      uu[(size_t)i] = (T*)u[i];
+      ff[(size_t)i] = f ? (const T*)f[i] : nullptr;
+    }
+    const double bco = (p && p->b != 0.0) ? p->b : 1.0 / 6.0;
+    const int ia = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsJacobi;
+    if (p && p->tile_x && p->tile_x != 32)
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "batched Jacobi tile_x = %d (supported 32)", p->tile_x);
+    return batched_jacobi_zmarch<T>(ctx, n, uu.data(), ff.data(), geoms.data(), h, nsweeps, bco, ia,
+                                    p ? p->tile_y : 0, p ? p->tile_z : 0, st);
+  }
   const int W = (p && p->tile_x) ? p->tile_x : (smoother == STENCIL_GS ? 16 : 32);
   const int H = (p && p->tile_y) ? p->tile_y : (smoother == STENCIL_GS ? 16 : 8);
   const int D = (p && p->tile_z) ? p->tile_z : (smoother == STENCIL_GS ? 16 : 8);

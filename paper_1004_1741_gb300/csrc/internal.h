@@ -79,6 +79,11 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
 template <typename T>
 int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
            const stencil_params* p, cudaStream_t st);
+// Batched Jacobi, one sweep per pass: one launch per sweep over all grids (batched_jacobi.cu)
+template <typename T>
+int batched_jacobi_zmarch(stencil_ctx* ctx, int n, T* const* u, const T* const* f, const Geom* geoms,
+                          const double* h, const int* nsweeps, double bco, int int_adds, int by, int zchunk,
+                          cudaStream_t st);
 // Jacobi in place without a second grid (jacobi_inplace.cu; stencil_params variant 6)
 template <typename T>
 int jacobi_inplace_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(32 * BY) jacobi_zmarch_kernel(const T* __restr
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(g.nz, z0 + zchunk);
   if (z0 >= z1) return;  // uniform over the block
-  zmarch_body<T, Ar, HAS_F, WEIGHTED, BY>(src, dst, f, g, z0, z1, c, sm);
+  zmarch_body<T, Ar, HAS_F, WEIGHTED, BY>(src, dst, f, g, z0, z1, c, sm, blockIdx.x, blockIdx.y);
 }
 
 // Pipelined variant: the same 2.5D z-march, but planes arrive in shared

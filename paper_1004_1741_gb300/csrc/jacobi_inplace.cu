@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(32 * BY) jacobi_slab_kernel(const T* __restric
       for (int z = 0; z < cb_planes; ++z) u[gs.at(x, y, cb_k0 + z)] = cb[(int64_t)z * gs.sy + o];
     }
   }
-  zmarch_body<T, Ar, HAS_F, WEIGHTED, BY>(src, dst, f, gs, 0, gs.nz, c, sm);
+  zmarch_body<T, Ar, HAS_F, WEIGHTED, BY>(src, dst, f, gs, 0, gs.nz, c, sm, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, class Ar, int BY>

@@ -14,15 +14,16 @@
 
 namespace stn {
 
-// The march of CTA (blockIdx.x, blockIdx.y) over planes [z0, z1) of g (z0 < z1,
-// the same for the whole CTA): src -> dst, sm the CTA's plane buffers.
+// The march of the CTA's tile (bx, by) (columns bx*32.., rows by*BY..) over
+// planes [z0, z1) of g (z0 < z1, the same for the whole CTA): src -> dst, sm
+// the CTA's plane buffers.
 template <typename T, class Ar, bool HAS_F, bool WEIGHTED, int BY>
 __device__ __forceinline__ void zmarch_body(const T* __restrict__ src, T* __restrict__ dst, const T* __restrict__ f,
                                             const Geom g, int z0, int z1, const Coef<T> c,
-                                            T (&sm)[2][BY + 2][32 + 2]) {
+                                            T (&sm)[2][BY + 2][32 + 2], int bx, int by) {
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x = blockIdx.x * 32 + tx;
-  const int y = blockIdx.y * BY + ty;
+  const int x = bx * 32 + tx;
+  const int y = by * BY + ty;
   const bool inside = (x <= g.nx) && (y <= g.ny);  // own column lies in the interior or the +1 halo
   const bool active = (x < g.nx) && (y < g.ny);    // own column is an interior column
   // halo duties (each at most one extra column or row)

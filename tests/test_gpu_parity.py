@@ -281,6 +281,34 @@ def test_batched_uneven_grids(ctx, smoother, dtype, nt):
         _assert_exact(us[i].cpu().numpy(), ofn(u0, f0, h, ns), "batched grid %d" % i)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("int_adds", [-1, 0, 5])
+def test_batched_jacobi_zmarch_many_grids(ctx, dtype, int_adds):
+    """Jacobi at nt = 1: one launch per sweep over every grid's tile columns; grids of ragged x/y tiles, a
+    column taller than one z-chunk (300 planes), grids that stop early and grids with and without f."""
+    dims = [(33, 5, 7), (1, 1, 300), (40, 9, 3), (31, 4, 1), (65, 13, 2)] + [(8 + i, 3 + i % 5, 2 + i % 7)
+                                                                          for i in range(40)]
+    grids = [W.random_grid(*d, seed=100 + i, dtype=dtype, with_f=(i % 3 != 1)) for i, d in enumerate(dims)]
+    hs = [W.grid_h(*d) for d in dims]
+    sweeps = [(3 * i) % 8 for i in range(len(dims))]
+    us = [_dev(u) for u, _ in grids]
+    fs = [_dev(f) for _, f in grids]
+    capi.stencil_batched(ctx, us, fs, hs, sweeps, capi.STENCIL_JACOBI, int_adds=int_adds)
+    torch.cuda.synchronize()
+    for i, ((u0, f0), h, ns) in enumerate(zip(grids, hs, sweeps)):
+        _assert_exact(us[i].cpu().numpy(), oracle.jacobi(u0, f0, h, ns), "batched Jacobi grid %d" % i)
+
+
+def test_batched_jacobi_task_variant_still_served(ctx):
+    """variant 3 keeps Jacobi at nt = 1 on the persistent tile tasks; both routes give the oracle's bits."""
+    u0, f0 = W.random_grid(37, 11, 13, seed=7, with_f=True)
+    ref = oracle.jacobi(u0, f0, 0.05, 3)
+    for variant in (0, 3):
+        us, fs = [_dev(u0)], [_dev(f0)]
+        capi.stencil_batched(ctx, us, fs, [0.05], [3], capi.STENCIL_JACOBI, nt=1, variant=variant)
+        _assert_exact(us[0].cpu().numpy(), ref, "batched Jacobi variant %d" % variant)
+
+
 @pytest.mark.parametrize("variant", [3, 5])
 def test_dataflow_wait_bound_reports_timeout(variant):
     """A task whose completion is never published: the bounded waits expire, the
