@@ -62,20 +62,33 @@ static cudaError_t bj_launch(int by, const BJGrid<T>* grids, int n, long long ct
   return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t bj_dispatch(int int_adds, int by, const BJGrid<T>* grids, int n, long long ctas,
-                               cudaStream_t st) {
+// pre: the grids' f arrays hold hh*f already (ArithPreF)
+template <typename T, template <class> class W>
+static cudaError_t bj_dispatch_w(int int_adds, int by, const BJGrid<T>* grids, int n, long long ctas,
+                                 cudaStream_t st) {
   if constexpr (sizeof(T) == 8) {
     switch (int_adds) {
-      case 1: return bj_launch<T, ArithF64Mix<0x1Du>>(by, grids, n, ctas, st);
-      case 2: return bj_launch<T, ArithF64Mix<0x15u>>(by, grids, n, ctas, st);
-      case 3: return bj_launch<T, ArithF64Mix<0x12u>>(by, grids, n, ctas, st);
-      case 4: return bj_launch<T, ArithF64Mix<0x10u>>(by, grids, n, ctas, st);
-      case 5: return bj_launch<T, ArithF64Mix<0x00u>>(by, grids, n, ctas, st);
+      case 1: return bj_launch<T, W<ArithF64Mix<0x1Du>>>(by, grids, n, ctas, st);
+      case 2: return bj_launch<T, W<ArithF64Mix<0x15u>>>(by, grids, n, ctas, st);
+      case 3: return bj_launch<T, W<ArithF64Mix<0x12u>>>(by, grids, n, ctas, st);
+      case 4: return bj_launch<T, W<ArithF64Mix<0x10u>>>(by, grids, n, ctas, st);
+      case 5: return bj_launch<T, W<ArithF64Mix<0x00u>>>(by, grids, n, ctas, st);
       default: break;
     }
   }
-  return bj_launch<T, typename DefaultArith<T>::type>(by, grids, n, ctas, st);
+  return bj_launch<T, W<typename DefaultArith<T>::type>>(by, grids, n, ctas, st);
+}
+
+template <class A>
+using Plain = A;
+
+template <typename T>
+static cudaError_t bj_dispatch(bool pre, int int_adds, int by, const BJGrid<T>* grids, int n, long long ctas,
+                               cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    if (pre) return bj_dispatch_w<T, ArithPreF>(int_adds, by, grids, n, ctas, st);
+  }
+  return bj_dispatch_w<T, Plain>(int_adds, by, grids, n, ctas, st);
 }
 
 template <typename T>
@@ -108,6 +121,30 @@ int batched_jacobi_zmarch(stencil_ctx* ctx, int n, T* const* u, const T* const* 
     first[(size_t)i] = odd ? ti : u[i];
     second[(size_t)i] = odd ? u[i] : ti;
   }
+  // FP64 with f over several sweeps: hh*f once per grid into workspace laid out like the second grids
+  // (one FP64 multiplication per site and sweep fewer); skipped when the budget has no room for it
+  std::vector<const T*> fuse((size_t)n);
+  for (int i = 0; i < n; ++i) fuse[(size_t)i] = f ? f[i] : nullptr;
+  bool pre = false;
+  if constexpr (sizeof(T) == 8) {
+    bool want = false;
+    for (int i = 0; i < n; ++i) want = want || (f && f[i] && nsweeps[i] >= 2);
+    double* w = want ? (double*)ws_try(ctx, SLOT_F_SCALED, total * sizeof(double)) : nullptr;
+    if (w) {
+      pre = true;
+      size_t o = 0;
+      for (int i = 0; i < n; ++i) {
+        const size_t cnt = (size_t)geoms[i].sy * (size_t)(geoms[i].nz + 2);
+        if (f && f[i] && nsweeps[i] > 0) {
+          cudaError_t e = prescale_f(f[i], w + o, cnt, h[i] * h[i], ctx->sm_count, st);
+          ctx->launches++;
+          if (e != cudaSuccess) return cuda_err(ctx, e, "prescale_f launch");
+          fuse[(size_t)i] = w + o;
+        }
+        o += cnt;
+      }
+    }
+  }
   // descriptors of every sweep's launch, uploaded once
   std::vector<BJGrid<T>> desc;
   std::vector<size_t> start((size_t)max_ns + 1, 0);
@@ -121,7 +158,7 @@ int batched_jacobi_zmarch(stencil_ctx* ctx, int n, T* const* u, const T* const* 
       BJGrid<T> d;
       d.src = (s % 2 == 0) ? first[(size_t)i] : second[(size_t)i];
       d.dst = (s % 2 == 0) ? second[(size_t)i] : first[(size_t)i];
-      d.f = f ? f[i] : nullptr;
+      d.f = fuse[(size_t)i];
       d.g = g;
       d.c.a = T(0);
       d.c.b = (T)bco;
@@ -146,7 +183,7 @@ int batched_jacobi_zmarch(stencil_ctx* ctx, int n, T* const* u, const T* const* 
     const int cnt = (int)(start[(size_t)s + 1] - start[(size_t)s]);
     if (cnt == 0 || ctas[(size_t)s] == 0) continue;
     if (ctas[(size_t)s] > 0x7FFFFFFFLL) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "batch too large for one launch");
-    e = bj_dispatch<T>(int_adds, by, ddesc + start[(size_t)s], cnt, ctas[(size_t)s], st);
+    e = bj_dispatch<T>(pre, int_adds, by, ddesc + start[(size_t)s], cnt, ctas[(size_t)s], st);
     ctx->launches++;
     if (e != cudaSuccess) return cuda_err(ctx, e, "batched_jacobi_kernel launch");
   }

@@ -22,6 +22,7 @@ namespace stn {
 struct ArithF64 {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double f_term(double hh, double fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ double add_k(double a, double b) { return add(a, b); }
 };
@@ -37,6 +38,7 @@ struct ArithF64Fma {
     asm("fma.rn.f64 %0, %1, %2, 0d8000000000000000;" : "=d"(r) : "d"(a), "d"(b));
     return r;
   }
+  static __device__ __forceinline__ double f_term(double hh, double fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ double add_k(double a, double b) { return add(a, b); }
 };
@@ -44,6 +46,7 @@ struct ArithF64Fma {
 struct ArithF32 {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float f_term(float hh, float fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ float add_k(float a, float b) { return add(a, b); }
 };
@@ -122,6 +125,7 @@ template <unsigned NATIVE_MASK>
 struct ArithF64Mix {
   static __device__ __forceinline__ double add(double a, double b) { return ArithF64Fma::add(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return ArithF64Fma::mul(a, b); }
+  static __device__ __forceinline__ double f_term(double hh, double fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ double add_k(double a, double b) {
     if (NATIVE_MASK & (1u << K)) return ArithF64Fma::add(a, b);
@@ -130,6 +134,15 @@ struct ArithF64Mix {
     if (K == 0 ? int_add_f64(a, b, &r) : int_add_f64_ge(a, b, &r)) return r;
     return ArithF64Fma::add(a, b);
   }
+};
+
+// The arithmetic A for a sweep whose f array already holds the products
+// hh*f (prescale_f: the same multiplication, once per call instead of once
+// per sweep): the site update adds f as it is.  Same bits.
+template <class A>
+struct ArithPreF : A {
+  template <typename T>
+  static __device__ __forceinline__ T f_term(T, T fv) { return fv; }
 };
 
 template <typename T>
@@ -159,7 +172,7 @@ __device__ __forceinline__ T site_update(T w, T e, T s, T n, T bo, T t, T fv, T 
   acc = Ar::template add_k<2>(acc, n);
   acc = Ar::template add_k<3>(acc, bo);
   acc = Ar::template add_k<4>(acc, t);
-  if (HAS_F) acc = Ar::add(acc, Ar::mul(c.hh, fv));
+  if (HAS_F) acc = Ar::add(acc, Ar::f_term(c.hh, fv));
   T v = Ar::mul(c.b, acc);
   if (WEIGHTED) v = Ar::add(Ar::mul(c.a, uc), v);
   return v;

@@ -28,6 +28,17 @@ int cuda_err(stencil_ctx* ctx, cudaError_t e, const char* where) {
   return set_err(ctx, STENCIL_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
+void* ws_try(stencil_ctx* ctx, SlotId id, size_t bytes) {
+  const Slot& s = ctx->slots[id];
+  if (s.bytes >= bytes && s.ptr) return s.ptr;
+  if (ctx->budget && ctx->held - s.bytes + bytes > ctx->budget) return nullptr;
+  const std::string saved = ctx->err;
+  int status;
+  void* p = ws_get(ctx, id, bytes, &status);
+  if (!p) ctx->err = saved;
+  return p;
+}
+
 void* ws_get(stencil_ctx* ctx, SlotId id, size_t bytes, int* status) {
   Slot& s = ctx->slots[id];
   *status = STENCIL_OK;

@@ -36,7 +36,8 @@ enum SlotId {
   SLOT_GS_GOFF,          // Gauss-Seidel site offsets for one grid shape
   SLOT_MG_LEVELS,        // multigrid: correction and right-hand side of every coarse level
   SLOT_MG_R,             // multigrid: residual of the level being restricted
-  SLOT_JACOBI_SLABS,     // in-place Jacobi: ring of two z-slabs of new values
+  SLOT_JACOBI_SLABS,     // in-place Jacobi: ring of three z-slabs of new values
+  SLOT_F_SCALED,         // FP64 sweeps with f: the products hh*f, computed once per call
   SLOT_COUNT
 };
 
@@ -70,6 +71,9 @@ int cuda_err(stencil_ctx* ctx, cudaError_t e, const char* where);
 // Returns a device buffer of at least `bytes` for slot `id` (growing it if
 // needed within the budget), or nullptr with ctx->err set.
 void* ws_get(stencil_ctx* ctx, SlotId id, size_t bytes, int* status);
+// The same for optional workspace: nullptr, and no error recorded, when the
+// budget or the device has no room (the caller then takes a path without it).
+void* ws_try(stencil_ctx* ctx, SlotId id, size_t bytes);
 int check_dims(stencil_ctx* ctx, const int64_t dims[3], Geom* g);
 
 // --- launchers (return STENCIL_* status) ---
@@ -79,6 +83,10 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
 template <typename T>
 int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
            const stencil_params* p, cudaStream_t st);
+// g[i] = hh * f[i] over n elements, with the site update's multiplication (ArithPreF sweeps then add g as
+// it is and give the same bits); one grid-stride launch on st.
+cudaError_t prescale_f(const double* f, double* g, size_t n, double hh, int sm_count, cudaStream_t st);
+
 // Batched Jacobi, one sweep per pass: one launch per sweep over all grids (batched_jacobi.cu)
 template <typename T>
 int batched_jacobi_zmarch(stencil_ctx* ctx, int n, T* const* u, const T* const* f, const Geom* geoms,

@@ -148,6 +148,43 @@ cudaError_t jacobi_sweep(const T* src, T* dst, const T* f, const Geom& g, int by
   return jacobi_sweep_ar<T, typename DefaultArith<T>::type>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
 }
 
+__global__ void __launch_bounds__(256) prescale_f_kernel(const double* __restrict__ f, double* __restrict__ g,
+                                                         double hh, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    g[i] = ArithF64Fma::mul(hh, f[i]);
+}
+
+cudaError_t prescale_f(const double* f, double* g, size_t n, double hh, int sm_count, cudaStream_t st) {
+  const size_t want = (n + 255) / 256;
+  const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>(want, (size_t)sm_count * 8));
+  prescale_f_kernel<<<blocks, 256, 0, st>>>(f, g, hh, n);
+  return cudaGetLastError();
+}
+
+// One unweighted FP64 z-march sweep whose f holds hh*f already (tile height 4 or 8).
+template <class Ar>
+static cudaError_t jacobi_sweep_pre_ar(const double* src, double* dst, const double* gf, const Geom& g, int by,
+                                       int zchunk, Coef<double> c, cudaStream_t st) {
+  dim3 grid((g.nx + 31) / 32, (g.ny + by - 1) / by, (g.nz + zchunk - 1) / zchunk);
+  if (by == 4)
+    jacobi_zmarch_kernel<double, ArithPreF<Ar>, true, false, 4><<<grid, dim3(32, 4), 0, st>>>(src, dst, gf, g, zchunk, c);
+  else
+    jacobi_zmarch_kernel<double, ArithPreF<Ar>, true, false, 8><<<grid, dim3(32, 8), 0, st>>>(src, dst, gf, g, zchunk, c);
+  return cudaGetLastError();
+}
+
+static cudaError_t jacobi_sweep_pre(const double* src, double* dst, const double* gf, const Geom& g, int by,
+                                    int zchunk, Coef<double> c, int int_adds, cudaStream_t st) {
+  switch (int_adds) {
+    case 1: return jacobi_sweep_pre_ar<ArithF64Mix<0x1Du>>(src, dst, gf, g, by, zchunk, c, st);
+    case 2: return jacobi_sweep_pre_ar<ArithF64Mix<0x15u>>(src, dst, gf, g, by, zchunk, c, st);
+    case 3: return jacobi_sweep_pre_ar<ArithF64Mix<0x12u>>(src, dst, gf, g, by, zchunk, c, st);
+    case 4: return jacobi_sweep_pre_ar<ArithF64Mix<0x10u>>(src, dst, gf, g, by, zchunk, c, st);
+    case 5: return jacobi_sweep_pre_ar<ArithF64Mix<0x00u>>(src, dst, gf, g, by, zchunk, c, st);
+    default: return jacobi_sweep_pre_ar<ArithF64Fma>(src, dst, gf, g, by, zchunk, c, st);
+  }
+}
+
 template <typename T>
 int tb_jacobi_run(stencil_ctx* ctx, T* u, T* tmp, const T* f, const Geom& g, double h, int nsweeps,
                   const stencil_params* p, cudaStream_t st);
@@ -260,11 +297,29 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   // the workspace grid carries the same halo as u
   cudaError_t e = cudaMemcpyAsync(tmp, u, bytes, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaMemcpyAsync(jacobi halo)");
+  // FP64 with f over several sweeps: hh*f once into workspace, the sweeps add it as it is (one FP64
+  // multiplication per site fewer; skipped when the workspace budget has no room for it)
+  const double* gf = nullptr;
+  if (sizeof(T) == 8 && f && nsweeps >= 2 && !weighted && !pipe && (by == 4 || by == 8)) {
+    const size_t n = (size_t)g.sy * (size_t)(g.nz + 2);
+    double* w = (double*)ws_try(ctx, SLOT_F_SCALED, n * sizeof(double));
+    if (w) {
+      e = prescale_f((const double*)f, w, n, (double)c.hh, ctx->sm_count, st);
+      ctx->launches++;
+      if (e != cudaSuccess) return cuda_err(ctx, e, "prescale_f launch");
+      gf = w;
+    }
+  }
   // ping-pong; with an odd count the first sweep reads the copy so the last lands in u
   T* a = (nsweeps % 2) ? tmp : u;
   T* b = (nsweeps % 2) ? u : tmp;
   for (int s = 0; s < nsweeps; ++s) {
-    e = jacobi_sweep<T>(a, b, f, g, by, zchunk, c, weighted, pipe, int_adds, st);
+    if constexpr (sizeof(T) == 8) {
+      if (gf) e = jacobi_sweep_pre((const double*)a, (double*)b, gf, g, by, zchunk, c, int_adds, st);
+      else e = jacobi_sweep<T>(a, b, f, g, by, zchunk, c, weighted, pipe, int_adds, st);
+    } else {
+      e = jacobi_sweep<T>(a, b, f, g, by, zchunk, c, weighted, pipe, int_adds, st);
+    }
     ctx->launches++;
     if (e != cudaSuccess) return cuda_err(ctx, e, "jacobi_zmarch_kernel launch");
     T* sw = a; a = b; b = sw;

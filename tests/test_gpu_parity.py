@@ -309,6 +309,26 @@ def test_batched_jacobi_task_variant_still_served(ctx):
         _assert_exact(us[0].cpu().numpy(), ref, "batched Jacobi variant %d" % variant)
 
 
+@pytest.mark.parametrize("int_adds", [-1, 0, 3])
+def test_jacobi_prescaled_f_and_budget_fallback(int_adds):
+    """FP64 with f over several sweeps: hh*f is computed once into workspace and the sweeps add it as it is;
+    a budget with no room for it keeps the multiplication in the sweeps.  Both give the oracle's bits."""
+    dims = (45, 19, 23)
+    u0, f0 = W.random_grid(*dims, seed=21, with_f=True)
+    u0 = u0 - 0.5  # mixed signs, as in a Poisson iterate
+    ref = oracle.jacobi(u0, f0, 0.03, 5)
+    grid_bytes = u0.nbytes
+    for budget, extra in ((0, 1), (int(grid_bytes * 1.5), 0)):
+        c = capi.Context(0, hbm_budget_bytes=budget)
+        u, f = _dev(u0), _dev(f0)
+        n0 = c.kernel_launches
+        capi.stencil_jacobi(c, u, f, 0.03, 5, int_adds=int_adds)
+        torch.cuda.synchronize()
+        assert c.kernel_launches - n0 == 5 + extra, "budget %d" % budget
+        _assert_exact(u.cpu().numpy(), ref, "prescaled f, budget %d" % budget)
+        c.close()
+
+
 @pytest.mark.parametrize("variant", [3, 5])
 def test_dataflow_wait_bound_reports_timeout(variant):
     """A task whose completion is never published: the bounded waits expire, the
