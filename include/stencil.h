@@ -36,7 +36,10 @@
  *  Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
  *  default stream).  Calls are stream-ordered and asynchronous unless they
  *  return a value through a host out-parameter, in which case they
- *  synchronise the stream before returning.
+ *  synchronise the stream before returning.  A context's workspace (second
+ *  grids, h^2 f products, task tables) is shared by its calls: calls on one
+ *  context must be ordered with each other (one stream, or streams the
+ *  caller orders with events); concurrent streams take a context each.
  *
  *  Errors.  Every int-returning call returns STENCIL_OK (0) or a negative
  *  STENCIL_ERR_* code; stencil_last_error(ctx) then describes the failure.
@@ -129,7 +132,12 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          are computed on the integer pipes (exact binary64 addition in
  *          integer arithmetic, falling back to the FP64 pipe for operands it
  *          does not cover): 0 = all on the FP64 pipe ... 5 = all five on
- *          the integer pipes; -1 = the library default.  Same bits whatever the value. */
+ *          the integer pipes; -1 = the library default.  Same bits whatever the value.
+ *  FP64 calls with f != NULL and at least two sweeps compute h^2 f once into
+ *  a further grid of workspace when the budget has room for it (Jacobi on the
+ *  z-march; Gauss-Seidel on the column march at int_adds 0 or 2; batched
+ *  calls alike) and add it as it is in every sweep: the same products, one
+ *  FP64 multiplication per site and sweep fewer. */
 typedef struct stencil_params {
   int nt;
   int tile_x, tile_y, tile_z;

@@ -38,8 +38,31 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
       fs[(size_t)i] = f ? (const T*)f[i] : nullptr;
     }
     const double bco = (p && p->b != 0.0) ? p->b : 1.0 / 6.0;
+    // FP64 with f over several sweeps: hh*f once per grid into workspace (one FP64 multiplication per site and
+    // sweep fewer; at int_adds 0 and 2, when the budget has room for it)
+    bool pre = false;
+    if constexpr (sizeof(T) == 8) {
+      bool want = ia == 0 || ia == 2;
+      bool some = false;
+      for (int i = 0; f && i < n; ++i) some = some || (f[i] && nsweeps[i] >= 2);
+      double* w = (want && some) ? (double*)ws_try(ctx, SLOT_F_SCALED, total * sizeof(double)) : nullptr;
+      if (w) {
+        pre = true;
+        size_t o = 0;
+        for (int i = 0; i < n; ++i) {
+          const size_t cnt = (size_t)geoms[(size_t)i].sy * (size_t)(geoms[(size_t)i].nz + 2);
+          if (fs[(size_t)i] && nsweeps[i] > 0) {
+            cudaError_t e = prescale_f(fs[(size_t)i], w + o, cnt, h[i] * h[i], ctx->sm_count, st);
+            ctx->launches++;
+            if (e != cudaSuccess) return cuda_err(ctx, e, "prescale_f launch");
+            fs[(size_t)i] = w + o;
+          }
+          o += cnt;
+        }
+      }
+    }
     return dataflow_run<T>(ctx, DF_KIND_GS_COLUMN, n, a.data(), nullptr, fs.data(), geoms.data(), nsweeps, h, cx, cy,
-                           cz, 1, ctx->df_timeout_ns, ctx->df_poison, st, (double)(T)bco, ia);
+                           cz, 1, ctx->df_timeout_ns, ctx->df_poison, st, (double)(T)bco, ia, pre);
   }
   // Jacobi with one sweep per pass: one z-march launch per sweep over all grids unless a task variant is asked for
   if (smoother == STENCIL_JACOBI && nt == 1 && (!p || p->variant == 0)) {

@@ -200,14 +200,14 @@ static int plan_build(stencil_ctx* ctx, DFPlan* pl, int kind, int n, const Geom*
 
 template <typename T>
 static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, int D, const SiteTable& tb,
-                        int int_adds, bool any_f) {
+                        int int_adds, bool any_f, bool pre_f) {
   cudaStream_t gs = ctx->gstream;
   cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamBeginCapture");
   int rc = STENCIL_OK;
   e = cudaMemsetAsync(pl->dev + pl->b_desc + pl->b_task, 0, pl->b_flag + 256, gs);
   if (e == cudaSuccess && kind == DF_KIND_GS_COLUMN) {
-    rc = df_column_launch<T>(ctx, pl->run, W, H, int_adds, any_f, gs);
+    rc = df_column_launch<T>(ctx, pl->run, W, H, int_adds, any_f, pre_f, gs);
   } else if (e == cudaSuccess) {
     rc = STENCIL_UNSUPPORTED_TILE;
 #define DF_TILE(WW, HH, DD)                                                                          \
@@ -246,7 +246,7 @@ static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, in
 template <typename T>
 int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, const T* const* f, const Geom* geoms,
                  const int* nsweeps, const double* h, int W, int H, int D, int nt, long long timeout_ns,
-                 long long poison, cudaStream_t st, double bco, int int_adds) {
+                 long long poison, cudaStream_t st, double bco, int int_adds, bool pre_f) {
   cudaError_t e;
   if (!ctx->gstream) {
     e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
@@ -264,7 +264,7 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
   bool any_f = false;
   for (int i = 0; f && i < n; ++i) any_f = any_f || f[i] != nullptr;
   // the column-march kernel's shared memory holds an f ring only when some grid has f
-  std::vector<long long> key = {(long long)sizeof(T), kind, n, W, H, D, nt, int_adds, any_f ? 1 : 0};
+  std::vector<long long> key = {(long long)sizeof(T), kind, n, W, H, D, nt, int_adds, any_f ? 1 : 0, pre_f ? 1 : 0};
   for (int i = 0; i < n; ++i) {
     key.push_back(geoms[i].nx);
     key.push_back(geoms[i].ny);
@@ -305,7 +305,7 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
   if (!pl->exec || pl->exec_timeout != timeout_ns || pl->exec_poison != poison || pl->exec_tb != tb.coords) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     pl->exec = nullptr;
-    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, tb, int_adds, any_f);
+    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, tb, int_adds, any_f, pre_f);
     if (rc) return rc;
     pl->exec_timeout = timeout_ns;
     pl->exec_poison = poison;
@@ -346,9 +346,9 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
 
 template int dataflow_run<double>(stencil_ctx*, int, int, double* const*, double* const*, const double* const*,
                                   const Geom*, const int*, const double*, int, int, int, int, long long, long long,
-                                  cudaStream_t, double, int);
+                                  cudaStream_t, double, int, bool);
 template int dataflow_run<float>(stencil_ctx*, int, int, float* const*, float* const*, const float* const*,
                                  const Geom*, const int*, const double*, int, int, int, int, long long, long long,
-                                 cudaStream_t, double, int);
+                                 cudaStream_t, double, int, bool);
 
 }  // namespace stn

@@ -343,6 +343,22 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
   if (int_adds < 0 || int_adds > 5)
     return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
   if constexpr (sizeof(T) == 8) {
+    // f over several sweeps: hh*f once into workspace, the sweeps add it as it is (one FP64 multiplication
+    // per site fewer; at int_adds 0 and 2, and only when the workspace budget has room for it)
+    if (f && nsweeps >= 2 && (int_adds == 0 || int_adds == 2)) {
+      const size_t n = (size_t)g.sy * (size_t)(g.nz + 2);
+      double* w = (double*)ws_try(ctx, SLOT_F_SCALED, n * sizeof(double));
+      if (w) {
+        cudaError_t e = prescale_f(f, w, n, (double)c.hh, ctx->sm_count, st);
+        ctx->launches++;
+        if (e != cudaSuccess) return cuda_err(ctx, e, "prescale_f launch");
+        if (int_adds == 2)
+          return gs_column_run<T, ArithPreF<ArithF64Mix<0x15u>>>(ctx, u, w, g, c, tx, ty, tz, nsweeps, persistent,
+                                                                 int_adds, h, st, true);
+        return gs_column_run<T, ArithPreF<ArithF64Fma>>(ctx, u, w, g, c, tx, ty, tz, nsweeps, persistent, int_adds,
+                                                        h, st, true);
+      }
+    }
     if (int_adds == 1) return gs_column_run<T, ArithF64Mix<0x1Du>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
     if (int_adds == 2) return gs_column_run<T, ArithF64Mix<0x15u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
     if (int_adds == 3) return gs_column_run<T, ArithF64Mix<0x12u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);

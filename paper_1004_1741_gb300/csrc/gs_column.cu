@@ -237,8 +237,14 @@ static int df_column_tile(stencil_ctx* ctx, const DFRun& run, int tx, int ty, bo
 }
 
 template <typename T>
-int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, cudaStream_t st) {
+int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, bool pre_f,
+                     cudaStream_t st) {
   if constexpr (sizeof(T) == 8) {
+    if (pre_f) {  // f holds hh*f
+      if (int_adds == 2) return df_column_tile<T, ArithPreF<ArithF64Mix<0x15u>>>(ctx, run, tx, ty, any_f, st);
+      if (int_adds == 0) return df_column_tile<T, ArithPreF<ArithF64Fma>>(ctx, run, tx, ty, any_f, st);
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "prescaled f with int_adds = %d (0 or 2)", int_adds);
+    }
     if (int_adds == 1) return df_column_tile<T, ArithF64Mix<0x1Du>>(ctx, run, tx, ty, any_f, st);
     if (int_adds == 2) return df_column_tile<T, ArithF64Mix<0x15u>>(ctx, run, tx, ty, any_f, st);
     if (int_adds == 3) return df_column_tile<T, ArithF64Mix<0x12u>>(ctx, run, tx, ty, any_f, st);
@@ -247,8 +253,8 @@ int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int
   }
   return df_column_tile<T, typename DefaultArith<T>::type>(ctx, run, tx, ty, any_f, st);
 }
-template int df_column_launch<double>(stencil_ctx*, const DFRun&, int, int, int, bool, cudaStream_t);
-template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, bool, cudaStream_t);
+template int df_column_launch<double>(stencil_ctx*, const DFRun&, int, int, int, bool, bool, cudaStream_t);
+template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, bool, bool, cudaStream_t);
 
 // Column-march Gauss-Seidel: tiles tx x ty columns (8x8, 8x16, 16x8; default 8x8 for FP64, whose FP64
 // pipe favours the short ramp of narrow tiles, 16x8 for FP32) x tz planes (default: equal chunks of at
@@ -256,7 +262,7 @@ template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, 
 // GPU while the march's ramp of tx + ty steps stays short against the chunk).  persistent: one dataflow launch (blocking) instead of one launch per level.
 template <typename T, class Ar>
 int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,
-                  int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st) {
+                  int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st, bool pre_f) {
   if (tx == 0) tx = sizeof(T) == 8 ? 8 : 16;
   if (ty == 0) ty = 8;
   if (tz <= 0) {
@@ -275,7 +281,7 @@ int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, 
     const int ns[1] = {nsweeps};
     const double hs[1] = {h};
     return dataflow_run<T>(ctx, DF_KIND_GS_COLUMN, 1, a, nullptr, fs, &g, ns, hs, tx, ty, tz, 1, ctx->df_timeout_ns,
-                           ctx->df_poison, st, (double)c.b, int_adds);
+                           ctx->df_poison, st, (double)c.b, int_adds, pre_f);
   }
 #define GS_COL(TXX, TYY)                                                                     \
   if (tx == TXX && ty == TYY)                                                                \
@@ -290,18 +296,22 @@ int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, 
 }
 
 template int gs_column_run<double, ArithF64Fma>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
-                                  int, int, bool, int, double, cudaStream_t);
+                                  int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<double, ArithF64Mix<0x1Du>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
-                                  int, int, bool, int, double, cudaStream_t);
+                                  int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<double, ArithF64Mix<0x15u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
-                                  int, int, bool, int, double, cudaStream_t);
+                                  int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<double, ArithF64Mix<0x12u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
-                                  int, int, bool, int, double, cudaStream_t);
+                                  int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<double, ArithF64Mix<0x10u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
-                                  int, int, bool, int, double, cudaStream_t);
+                                  int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<double, ArithF64Mix<0x00u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
-                                  int, int, bool, int, double, cudaStream_t);
+                                  int, int, bool, int, double, cudaStream_t, bool);
+template int gs_column_run<double, ArithPreF<ArithF64Fma>>(stencil_ctx*, double*, const double*, const Geom&,
+                                  Coef<double>, int, int, int, int, bool, int, double, cudaStream_t, bool);
+template int gs_column_run<double, ArithPreF<ArithF64Mix<0x15u>>>(stencil_ctx*, double*, const double*, const Geom&,
+                                  Coef<double>, int, int, int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<float, ArithF32>(stencil_ctx*, float*, const float*, const Geom&, Coef<float>, int, int,
-                                  int, int, bool, int, double, cudaStream_t);
+                                  int, int, bool, int, double, cudaStream_t, bool);
 
 }  // namespace stn

@@ -96,10 +96,11 @@ int batched_jacobi_zmarch(stencil_ctx* ctx, int n, T* const* u, const T* const* 
 template <typename T>
 int jacobi_inplace_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
                        const stencil_params* p, cudaStream_t st);
-// column-march Gauss-Seidel, one sweep per task (gs_column.cu); zero tile extents: defaults
+// column-march Gauss-Seidel, one sweep per task (gs_column.cu); zero tile extents: defaults; pre_f: f holds
+// hh*f (Ar is then an ArithPreF, and the persistent form takes int_adds 0 or 2)
 template <typename T, class Ar>
 int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,
-                  int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st);
+                  int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st, bool pre_f = false);
 
 // Residual r = f - A u; optional FP64 r and/or FP32 r32 on the interior;
 // sums of r^2 and f^2 into the context's result slot (device) when `norm`
@@ -127,13 +128,16 @@ void dataflow_release(stencil_ctx* ctx);  // internal: no kernel instantiated fo
 template <typename T>
 int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, const T* const* f, const Geom* geoms,
                  const int* nsweeps, const double* h, int W, int H, int D, int nt, long long timeout_ns,
-                 long long poison, cudaStream_t st, double bco = 1.0 / 6.0, int int_adds = 0);
+                 long long poison, cudaStream_t st, double bco = 1.0 / 6.0, int int_adds = 0,
+                 bool pre_f = false);
 // task kind of dataflow_run beside STENCIL_JACOBI / STENCIL_GS: the column-march
 // Gauss-Seidel task (gs_column.cu; nt = 1, tile W x H columns x D planes)
 constexpr int DF_KIND_GS_COLUMN = 16;
 struct DFRun;
 // launch of the persistent column-march kernel for one dataflow run (gs_column.cu)
 template <typename T>
-int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, cudaStream_t st);
+// (pre_f: the grids' f arrays hold hh*f; offered at int_adds 0 and 2)
+int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, bool pre_f,
+                     cudaStream_t st);
 
 }  // namespace stn

@@ -309,24 +309,48 @@ def test_batched_jacobi_task_variant_still_served(ctx):
         _assert_exact(us[0].cpu().numpy(), ref, "batched Jacobi variant %d" % variant)
 
 
-@pytest.mark.parametrize("int_adds", [-1, 0, 3])
-def test_jacobi_prescaled_f_and_budget_fallback(int_adds):
-    """FP64 with f over several sweeps: hh*f is computed once into workspace and the sweeps add it as it is;
-    a budget with no room for it keeps the multiplication in the sweeps.  Both give the oracle's bits."""
+@pytest.mark.parametrize("case", [("jacobi", -1, 0), ("jacobi", 0, 0), ("jacobi", 3, 0), ("gs", -1, 0),
+                                  ("gs", 0, 0), ("gs", 2, 5), ("gs", -1, 5), ("gs", 3, 0)])
+def test_prescaled_f_and_budget_fallback(case):
+    """FP64 with f over several sweeps: hh*f is computed once into workspace and the sweeps add it as it is
+    (one launch more); a budget with no room for it keeps the multiplication in the sweeps.  Both give the
+    oracle's bits (Gauss-Seidel int_adds 3 has no prescaled form: no extra launch either way)."""
+    smoother, int_adds, variant = case
     dims = (45, 19, 23)
     u0, f0 = W.random_grid(*dims, seed=21, with_f=True)
     u0 = u0 - 0.5  # mixed signs, as in a Poisson iterate
-    ref = oracle.jacobi(u0, f0, 0.03, 5)
-    grid_bytes = u0.nbytes
-    for budget, extra in ((0, 1), (int(grid_bytes * 1.5), 0)):
+    fn, ofn = (capi.stencil_jacobi, oracle.jacobi) if smoother == "jacobi" else (capi.stencil_gs_lex, oracle.gs_lex)
+    ref = ofn(u0, f0, 0.03, 5)
+    launches = []
+    # Jacobi needs a second grid of workspace, Gauss-Seidel only small task tables
+    for budget in (0, int(u0.nbytes * (1.5 if smoother == "jacobi" else 0.9))):
         c = capi.Context(0, hbm_budget_bytes=budget)
         u, f = _dev(u0), _dev(f0)
         n0 = c.kernel_launches
-        capi.stencil_jacobi(c, u, f, 0.03, 5, int_adds=int_adds)
+        fn(c, u, f, 0.03, 5, int_adds=int_adds, variant=variant)
         torch.cuda.synchronize()
-        assert c.kernel_launches - n0 == 5 + extra, "budget %d" % budget
-        _assert_exact(u.cpu().numpy(), ref, "prescaled f, budget %d" % budget)
+        launches.append(c.kernel_launches - n0)
+        _assert_exact(u.cpu().numpy(), ref, "%s budget %d" % (case, budget))
         c.close()
+    prescaled = not (smoother == "gs" and int_adds == 3)
+    assert launches[0] - launches[1] == (1 if prescaled else 0), launches
+
+
+def test_batched_prescaled_f(ctx):
+    """Batched FP64 Poisson grids (Jacobi z-march and Gauss-Seidel column tasks) with prescaled f, grids with
+    and without f and one-sweep grids in the mix."""
+    dims = [(40, 12, 9), (17, 5, 30), (9, 33, 7), (64, 8, 5)]
+    grids = [W.random_grid(*d, seed=60 + i, with_f=(i != 2)) for i, d in enumerate(dims)]
+    grids = [(u - 0.5, f) for u, f in grids]
+    hs = [W.grid_h(*d) for d in dims]
+    sweeps = [4, 1, 3, 6]
+    for sm, ofn in ((capi.STENCIL_JACOBI, oracle.jacobi), (capi.STENCIL_GS, oracle.gs_lex)):
+        us = [_dev(u) for u, _ in grids]
+        fs = [_dev(f) for _, f in grids]
+        capi.stencil_batched(ctx, us, fs, hs, sweeps, sm)
+        torch.cuda.synchronize()
+        for i, ((u0, f0), h, ns) in enumerate(zip(grids, hs, sweeps)):
+            _assert_exact(us[i].cpu().numpy(), ofn(u0, f0, h, ns), "batched %d grid %d" % (sm, i))
 
 
 @pytest.mark.parametrize("variant", [3, 5])
