@@ -470,7 +470,8 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
 
 
 def run_case(args):
-    """One smoother on an n^3 grid (halo seed 1, interior seed 2; --poisson adds f ~ N(0,1)):
+    """One smoother on an n^3 grid (halo seed 1, interior seed 2, or zero with --zero-u; --poisson
+    adds f ~ N(0,1)):
     one untimed call (workspace, plans, graphs), then --repeat calls of --sweeps sweeps timed
     with CUDA events: the small case for profiler captures and single-configuration timings."""
     import numpy as np
@@ -491,6 +492,8 @@ def run_case(args):
         ctx.close()
         return 0
     u = torch.from_numpy(workloads.laplace_cube(args.n)).to("cuda")
+    if args.zero_u:
+        u.zero_()
     dt = torch.float32 if args.dtype == "f32" else torch.float64
     u = u.to(dt)
     f = None
@@ -514,7 +517,8 @@ def run_case(args):
     ms = a.elapsed_time(b)
     print(json.dumps({"case": args.case, "n": args.n, "sweeps": args.sweeps, "nt": args.nt, "repeat": args.repeat,
                       "variant": args.variant, "int_adds": args.int_adds, "dtype": args.dtype,
-                      "poisson": bool(args.poisson), "launches": ctx.kernel_launches - n0, "ms": ms,
+                      "poisson": bool(args.poisson), "zero_u": bool(args.zero_u),
+                      "launches": ctx.kernel_launches - n0, "ms": ms,
                       "glups": args.n ** 3 * args.sweeps * args.repeat / ms / 1e6,
                       "workspace_mb": ctx.workspace_bytes / 1e6}))
     ctx.close()
@@ -709,6 +713,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="kernel variant of the profiling case")
     ap.add_argument("--int-adds", type=int, default=-1, help="integer-pipe additions of the profiling case")
     ap.add_argument("--poisson", action="store_true", help="profiling case with f ~ N(0,1) instead of f = 0")
+    ap.add_argument("--zero-u", action="store_true",
+                    help="profiling case from u = 0 (halo too): with --poisson the iterates take both signs")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--suite", choices=["mixed", "served", "mg"], help="a secondary workload instead of the headline")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000")
