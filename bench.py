@@ -28,10 +28,12 @@ if ROOT not in sys.path:
 
 N = 400
 SWEEPS = 100
-# the launch configuration timed for the headline (tests/test_gpu_parity.py checks it at full size)
+# the launch configuration timed for the headline (tests/test_gpu_parity.py checks it at full size);
+# int_adds: the fixed integer-pipe additions measured fastest on this positive data (the library's
+# default, the adaptive form, pays a warp vote per update for data of both signs)
 HEADLINE = {
-    "jacobi": {"nt": 1, "tile": (32, 4, 0), "variant": 0},
-    "gs": {"nt": 1, "tile": (8, 8, 0), "variant": 5},
+    "jacobi": {"nt": 1, "tile": (32, 4, 0), "variant": 0, "int_adds": 3},
+    "gs": {"nt": 1, "tile": (8, 8, 0), "variant": 5, "int_adds": 2},
 }
 NT_SWEEP = [1, 2, 4, 8, 16]
 METRIC = "GLUP/s at 400^3 FP64 (Jacobi, GS) vs HBM roofline; batched/served vs plain, p99"
@@ -242,12 +244,12 @@ def run_gpu(args):
         if timed:
             ev["j"][0].record(stream)
         capi.stencil_jacobi(ctx, uj, None, 1.0, SWEEPS, nt=cj["nt"], tile=cj["tile"], variant=cj["variant"],
-                            stream=stream)
+                            int_adds=cj["int_adds"], stream=stream)
         if timed:
             ev["j"][1].record(stream)
             ev["g"][0].record(stream)
         capi.stencil_gs_lex(ctx, ug, None, 1.0, SWEEPS, nt=cg["nt"], tile=cg["tile"], variant=cg["variant"],
-                            stream=stream)
+                            int_adds=cg["int_adds"], stream=stream)
         if timed:
             ev["g"][1].record(stream)
         rj = capi.residual_norm(ctx, uj, None, 1.0, stream=stream)
@@ -338,8 +340,10 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "jacobi+gs 400^3 fp64, 100 sweeps each + residual norms", "n": N,
                        "sweeps": SWEEPS,
-                       "jacobi": {"nt": cj["nt"], "tile": list(cj["tile"]), "variant": cj["variant"]},
-                       "gs": {"nt": cg["nt"], "tile": list(cg["tile"]), "variant": cg["variant"]}, "parallelism": "replicas" if world > 1 else "1gpu",
+                       "jacobi": {"nt": cj["nt"], "tile": list(cj["tile"]), "variant": cj["variant"],
+                                  "int_adds": cj["int_adds"]},
+                       "gs": {"nt": cg["nt"], "tile": list(cg["tile"]), "variant": cg["variant"],
+                              "int_adds": cg["int_adds"]}, "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "inputs larger than L2 (2 x 512.6 MB vs 129 MB); no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "details": details,
@@ -378,10 +382,11 @@ def nt_sweep(ctx, capi, torch, uj, ug, stream):
             try:
                 tile = cfg["tile"] if nt == cfg["nt"] else (0, 0, 0)
                 variant = cfg["variant"] if nt == cfg["nt"] else 0
-                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, variant=variant, stream=stream)  # warm
+                ia = cfg["int_adds"] if nt == cfg["nt"] else -1
+                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, variant=variant, int_adds=ia, stream=stream)  # warm
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, variant=variant, stream=stream)
+                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, variant=variant, int_adds=ia, stream=stream)
                 b.record(stream)
                 torch.cuda.synchronize()
                 t = a.elapsed_time(b) / 1e3
@@ -446,9 +451,9 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
         dj.copy_(hj, non_blocking=True)
         dg.copy_(hg, non_blocking=True)
         capi.stencil_jacobi(ctx, dj, None, 1.0, SWEEPS, nt=cj["nt"], tile=cj["tile"], variant=cj["variant"],
-                            stream=stream)
+                            int_adds=cj["int_adds"], stream=stream)
         capi.stencil_gs_lex(ctx, dg, None, 1.0, SWEEPS, nt=cg["nt"], tile=cg["tile"], variant=cg["variant"],
-                            stream=stream)
+                            int_adds=cg["int_adds"], stream=stream)
         capi.residual_norm(ctx, dj, None, 1.0, stream=stream)
         capi.residual_norm(ctx, dg, None, 1.0, stream=stream)
         oj.copy_(dj, non_blocking=True)

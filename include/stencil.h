@@ -130,12 +130,19 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          Every variant gives the same bits.
  *  int_adds FP64 only: how many of the five additions of the neighbour sum
  *          are computed on the integer pipes (exact binary64 addition in
- *          integer arithmetic, falling back to the FP64 pipe for operands it
- *          does not cover): 0 = all on the FP64 pipe ... 5 = all five on
- *          the integer pipes; -1 = the library default.  Same bits whatever the value.
+ *          integer arithmetic for positive operands, falling back to the
+ *          FP64 pipe for operands it does not cover): 0 = all on the FP64
+ *          pipe ... 5 = all five on the integer pipes; 6 = adaptive: per warp
+ *          and update, 3 (Jacobi z-march) or 2 (column march) integer-pipe
+ *          additions when every neighbour is non-negative, else the additions
+ *          on the FP64 pipe and the multiplication by b in exact integer
+ *          arithmetic (Poisson iterates take both signs); -1 = the library
+ *          default: 6 on the Jacobi z-march (also in place and batched) and
+ *          the Gauss-Seidel column march, 1 on the other Gauss-Seidel paths
+ *          (which take 6 as 1).  Same bits whatever the value.
  *  FP64 calls with f != NULL and at least two sweeps compute h^2 f once into
  *  a further grid of workspace when the budget has room for it (Jacobi on the
- *  z-march; Gauss-Seidel on the column march at int_adds 0 or 2; batched
+ *  z-march; Gauss-Seidel on the column march at int_adds 0, 2 or 6; batched
  *  calls alike) and add it as it is in every sweep: the same products, one
  *  FP64 multiplication per site and sweep fewer. */
 typedef struct stencil_params {
@@ -321,12 +328,14 @@ int stencil_server_stats_get(stencil_server* srv, stencil_server_stats* out);
 /* Stops the worker after the current round and frees everything. */
 void stencil_server_destroy(stencil_server* srv);
 
-/* Self-check of the integer-pipe binary64 addition: n pairs drawn from a
- * counter-based generator seeded by `seed` (random magnitudes, ties, carries,
- * zeros, signs), each summed on the integer pipes (the symmetric form, and the
- * ordered form in both argument orders) and on the FP64 pipe.  *out_mismatch
- * (host) receives the number of integer-pipe sums whose bits differ (must be
- * 0), *out_fast the number of pairs the symmetric form handled.  Blocking. */
+/* Self-check of the integer-arithmetic binary64 addition and multiplication:
+ * n pairs drawn from a counter-based generator seeded by `seed` (random
+ * magnitudes, ties, carries, zeros, signs), each summed on the integer pipes
+ * (the symmetric form, and the ordered form in both argument orders) and
+ * multiplied in integer arithmetic (both orders, random signs), against the
+ * FP64 pipe.  *out_mismatch (host) receives the number of results whose bits
+ * differ (must be 0), *out_fast the number of pairs the symmetric addition
+ * handled.  Blocking. */
 int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t seed, uint64_t* out_mismatch,
                              uint64_t* out_fast);
 

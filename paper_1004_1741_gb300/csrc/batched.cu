@@ -30,7 +30,7 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
     const int cy = (p && p->tile_y) ? p->tile_y : 8;
     const int cz = (p && p->tile_z) ? p->tile_z : 100;
     const int ia = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsColumn;
-    if (ia > 5) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", ia);
+    if (ia > kIntAddsAdaptive) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..6)", ia);
     std::vector<T*> a((size_t)n);
     std::vector<const T*> fs((size_t)n);
     for (int i = 0; i < n; ++i) {
@@ -39,10 +39,10 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
     }
     const double bco = (p && p->b != 0.0) ? p->b : 1.0 / 6.0;
     // FP64 with f over several sweeps: hh*f once per grid into workspace (one FP64 multiplication per site and
-    // sweep fewer; at int_adds 0 and 2, when the budget has room for it)
+    // sweep fewer; at int_adds 0, 2 and 6, when the budget has room for it)
     bool pre = false;
     if constexpr (sizeof(T) == 8) {
-      bool want = ia == 0 || ia == 2;
+      bool want = ia == 0 || ia == 2 || ia == kIntAddsAdaptive;
       bool some = false;
       for (int i = 0; f && i < n; ++i) some = some || (f[i] && nsweeps[i] >= 2);
       double* w = (want && some) ? (double*)ws_try(ctx, SLOT_F_SCALED, total * sizeof(double)) : nullptr;

@@ -73,6 +73,8 @@ static cudaError_t bj_dispatch_w(int int_adds, int by, const BJGrid<T>* grids, i
       case 3: return bj_launch<T, W<ArithF64Mix<0x12u>>>(by, grids, n, ctas, st);
       case 4: return bj_launch<T, W<ArithF64Mix<0x10u>>>(by, grids, n, ctas, st);
       case 5: return bj_launch<T, W<ArithF64Mix<0x00u>>>(by, grids, n, ctas, st);
+      case kIntAddsAdaptive:
+        return bj_launch<T, ArithAdaptive<W<ArithF64Mix<0x12u>>, W<ArithF64Mix<0x1Fu, true>>>>(by, grids, n, ctas, st);
       default: break;
     }
   }
@@ -95,8 +97,8 @@ template <typename T>
 int batched_jacobi_zmarch(stencil_ctx* ctx, int n, T* const* u, const T* const* f, const Geom* geoms,
                           const double* h, const int* nsweeps, double bco, int int_adds, int by, int zchunk,
                           cudaStream_t st) {
-  if (int_adds < 0 || int_adds > 5)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
+  if (int_adds < 0 || int_adds > kIntAddsAdaptive)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..6)", int_adds);
   if (by == 0) by = sizeof(T) == 8 ? 4 : 8;
   if (by != 4 && by != 8) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "batched Jacobi tile_y = %d (4 or 8)", by);
   if (zchunk < 0) return set_err(ctx, STENCIL_ERR_ARG, "tile_z < 0");

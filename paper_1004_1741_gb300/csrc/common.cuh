@@ -22,6 +22,7 @@ namespace stn {
 struct ArithF64 {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double mul_b(double b, double s) { return mul(b, s); }
   static __device__ __forceinline__ double f_term(double hh, double fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ double add_k(double a, double b) { return add(a, b); }
@@ -39,6 +40,7 @@ struct ArithF64Fma {
     return r;
   }
   static __device__ __forceinline__ double f_term(double hh, double fv) { return mul(hh, fv); }
+  static __device__ __forceinline__ double mul_b(double b, double s) { return mul(b, s); }
   template <int K>
   static __device__ __forceinline__ double add_k(double a, double b) { return add(a, b); }
 };
@@ -46,6 +48,7 @@ struct ArithF64Fma {
 struct ArithF32 {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float mul_b(float b, float s) { return mul(b, s); }
   static __device__ __forceinline__ float f_term(float hh, float fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ float add_k(float a, float b) { return add(a, b); }
@@ -117,14 +120,52 @@ __device__ __forceinline__ bool int_add_f64_ge(double a, double b, double* out) 
   return true;
 }
 
+// Binary64 multiplication carried out in integer arithmetic (the 64-bit
+// products on the integer multiply-add path, the rest on the ALU pipe): the
+// IEEE round-to-nearest-even product when both operands are normal and the
+// product's exponent stays in the normal range; otherwise it reports failure
+// and the caller uses the FP64 pipe.  Method: the significands (implicit bit
+// set, 53 bits) give a 106-bit product P in [2^104, 2^106); with one operand
+// pre-shifted by 11, the high 64 bits of the 128-bit product are P / 2^53 and
+// the low 64 bits hold P's remaining 53 bits at the top.  A product of two or
+// more keeps the high word as its significand, a smaller one takes the next
+// bit from the low word; the first dropped bit and the OR of the rest round to
+// nearest with ties to even; a carry out of the rounding ripples into the
+// exponent (a carry into the exponent's all-ones code reports failure).
+__device__ __forceinline__ bool int_mul_f64(double a, double b, double* out) {
+  const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+  const unsigned ea = (unsigned)(A >> 52) & 0x7FFu, eb = (unsigned)(B >> 52) & 0x7FFu;
+  const int e = (int)ea + (int)eb - 1023;  // exponent field of a product in [1, 2)
+  if (ea - 1u >= 2046u || eb - 1u >= 2046u || (unsigned)(e - 1) >= 2045u) return false;
+  const unsigned long long FRAC = 0xFFFFFFFFFFFFFull, IMPL = 1ull << 52;
+  const unsigned long long ma = ((A & FRAC) | IMPL) << 11, mb = (B & FRAC) | IMPL;
+  const unsigned long long hi = __umul64hi(ma, mb), lo = ma * mb;
+  const unsigned c = (unsigned)(hi >> 52);  // 1: the product is at least 2
+  const unsigned long long mant = c ? hi : (hi << 1) | (lo >> 63);
+  const unsigned long long rb = c ? (lo >> 63) : ((lo >> 62) & 1ull);
+  const unsigned long long sticky = (c ? (lo << 1) : (lo << 2)) != 0ull;
+  const unsigned long long m2 = mant + (rb & (sticky | (mant & 1ull)));
+  const unsigned long long res = m2 + ((unsigned long long)(e + (int)c - 1) << 52);
+  if (((res >> 52) & 0x7FFull) == 0x7FFull) return false;
+  *out = __longlong_as_double((long long)(res | ((A ^ B) & (1ull << 63))));
+  return true;
+}
+
 // FP64 arithmetic that splits the additions of a site update between the
 // integer pipes (int_add_f64) and the FP64 pipe: the additions whose bit is
 // set in NATIVE_MASK (0 = first, 4 = last of the neighbour sum) and every
 // multiplication go to the FP64 pipe.  Same bits as ArithF64 either way.
-template <unsigned NATIVE_MASK>
+template <unsigned NATIVE_MASK, bool INT_MUL = false>
 struct ArithF64Mix {
   static __device__ __forceinline__ double add(double a, double b) { return ArithF64Fma::add(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return ArithF64Fma::mul(a, b); }
+  // the bracket's weight times the bracket, on the integer path when INT_MUL
+  static __device__ __forceinline__ double mul_b(double b, double s) {
+    double r;
+    if (INT_MUL && int_mul_f64(b, s, &r)) return r;
+    return ArithF64Fma::mul(b, s);
+  }
   static __device__ __forceinline__ double f_term(double hh, double fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ double add_k(double a, double b) {
@@ -143,6 +184,25 @@ template <class A>
 struct ArithPreF : A {
   template <typename T>
   static __device__ __forceinline__ T f_term(T, T fv) { return fv; }
+};
+
+// Data-dependent choice per warp and update: POS for neighbourhoods that are
+// all non-negative (integer-pipe additions apply), MIXED otherwise (additions
+// on the FP64 pipe, the multiplication on the integer path).  The kernel body
+// takes the vote (site_update_adaptive); every other operation uses POS.
+template <class POS, class MIXED>
+struct ArithAdaptive : POS {
+  using Pos = POS;
+  using Mixed = MIXED;
+};
+
+template <class Ar>
+struct AdaptOf {
+  static constexpr bool on = false;
+};
+template <class P, class M>
+struct AdaptOf<ArithAdaptive<P, M>> {
+  static constexpr bool on = true;
 };
 
 template <typename T>
@@ -173,9 +233,26 @@ __device__ __forceinline__ T site_update(T w, T e, T s, T n, T bo, T t, T fv, T 
   acc = Ar::template add_k<3>(acc, bo);
   acc = Ar::template add_k<4>(acc, t);
   if (HAS_F) acc = Ar::add(acc, Ar::f_term(c.hh, fv));
-  T v = Ar::mul(c.b, acc);
+  T v = Ar::mul_b(c.b, acc);
   if (WEIGHTED) v = Ar::add(Ar::mul(c.a, uc), v);
   return v;
+}
+
+// site_update for the whole warp (every lane must call it; `active` lanes
+// get their update): with an ArithAdaptive the warp takes POS when every
+// active lane's six neighbours have their sign bit clear, else MIXED.
+template <typename T, class Ar, bool HAS_F, bool WEIGHTED>
+__device__ __forceinline__ T site_update_warp(bool active, T w, T e, T s, T n, T bo, T t, T fv, T uc,
+                                              const Coef<T>& c) {
+  if constexpr (AdaptOf<Ar>::on && sizeof(T) == 8) {
+    const int sg = __double2hiint(w) | __double2hiint(e) | __double2hiint(s) | __double2hiint(n) |
+                   __double2hiint(bo) | __double2hiint(t);
+    if (__all_sync(0xFFFFFFFFu, !active || sg >= 0))
+      return active ? site_update<T, typename Ar::Pos, HAS_F, WEIGHTED>(w, e, s, n, bo, t, fv, uc, c) : T(0);
+    return active ? site_update<T, typename Ar::Mixed, HAS_F, WEIGHTED>(w, e, s, n, bo, t, fv, uc, c) : T(0);
+  } else {
+    return active ? site_update<T, Ar, HAS_F, WEIGHTED>(w, e, s, n, bo, t, fv, uc, c) : T(0);
+  }
 }
 
 // Asynchronous element copy global -> shared (cp.async, through L1) and its

@@ -340,18 +340,21 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
   const int tx = p ? p->tile_x : 0, ty = p ? p->tile_y : 0, tz = p ? p->tile_z : 0;
   const bool persistent = p && p->variant == 5;
   const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsColumn;
-  if (int_adds < 0 || int_adds > 5)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
+  if (int_adds < 0 || int_adds > kIntAddsAdaptive)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..6)", int_adds);
   if constexpr (sizeof(T) == 8) {
     // f over several sweeps: hh*f once into workspace, the sweeps add it as it is (one FP64 multiplication
-    // per site fewer; at int_adds 0 and 2, and only when the workspace budget has room for it)
-    if (f && nsweeps >= 2 && (int_adds == 0 || int_adds == 2)) {
+    // per site fewer; at int_adds 0, 2 and 6, and only when the workspace budget has room for it)
+    if (f && nsweeps >= 2 && (int_adds == 0 || int_adds == 2 || int_adds == kIntAddsAdaptive)) {
       const size_t n = (size_t)g.sy * (size_t)(g.nz + 2);
       double* w = (double*)ws_try(ctx, SLOT_F_SCALED, n * sizeof(double));
       if (w) {
         cudaError_t e = prescale_f(f, w, n, (double)c.hh, ctx->sm_count, st);
         ctx->launches++;
         if (e != cudaSuccess) return cuda_err(ctx, e, "prescale_f launch");
+        if (int_adds == kIntAddsAdaptive)
+          return gs_column_run<T, AdaptColumnPre>(ctx, u, w, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st,
+                                                  true);
         if (int_adds == 2)
           return gs_column_run<T, ArithPreF<ArithF64Mix<0x15u>>>(ctx, u, w, g, c, tx, ty, tz, nsweeps, persistent,
                                                                  int_adds, h, st, true);
@@ -364,6 +367,8 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
     if (int_adds == 3) return gs_column_run<T, ArithF64Mix<0x12u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
     if (int_adds == 4) return gs_column_run<T, ArithF64Mix<0x10u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
     if (int_adds == 5) return gs_column_run<T, ArithF64Mix<0x00u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+    if (int_adds == kIntAddsAdaptive)
+      return gs_column_run<T, AdaptColumn>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
   }
   return gs_column_run<T, typename DefaultArith<T>::type>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
 }
@@ -404,9 +409,10 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
   c.a = T(0);
   c.b = (T)((p && p->b != 0.0) ? p->b : 1.0 / 6.0);
   c.hh = (T)(h * h);
-  const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAdds;
+  // the adaptive form is the column march's: these tiles take their own default for it
+  const int int_adds = (p && p->int_adds >= 0 && p->int_adds != kIntAddsAdaptive) ? p->int_adds : kDefaultIntAdds;
   if (int_adds < 0 || int_adds > 5)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..6)", int_adds);
   if constexpr (sizeof(T) == 8) {
     if (int_adds == 1) return gs_tiles<T, ArithF64Mix<0x1Du>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);
     if (int_adds == 2) return gs_tiles<T, ArithF64Mix<0x15u>>(ctx, u, f, g, c, tx, ty, tz, nt, nsweeps, direct, st);

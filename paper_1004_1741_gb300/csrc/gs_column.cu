@@ -110,7 +110,16 @@ __device__ __forceinline__ void gs_column_body(T* u, const T* __restrict__ f, co
     if (ldy && inwin(t, lo_y, hi_y)) cp_async_elem(ycell + sl * PL, gy);
     if (HAS_F && comp && inwin(t, lo_f, hi_f)) cp_async_elem(fcell + sl * FPL, gf);
     cp_async_commit();
-    if (comp && inwin(t, lo_c, hi_c)) {
+    if constexpr (AdaptOf<Ar>::on) {  // the whole warp votes (t is uniform; every ring read stays in the ring)
+      const bool upd = comp && inwin(t, lo_c, hi_c);
+      const int sm1 = st == 0 ? R - 1 : st - 1, sp1 = wrap(st);
+      const T* pm = cell + sm1 * PL;
+      const T* pp = cell + sp1 * PL;
+      const T fv = HAS_F ? fcell[st * FPL] : T(0);
+      const T v = site_update_warp<T, Ar, HAS_F, false>(upd, pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv, T(0),
+                                                        c);
+      if (upd) cell[st * PL] = v;
+    } else if (comp && inwin(t, lo_c, hi_c)) {
       const int sm1 = st == 0 ? R - 1 : st - 1, sp1 = wrap(st);
       const T* pm = cell + sm1 * PL;
       const T* pp = cell + sp1 * PL;
@@ -241,10 +250,12 @@ int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int
                      cudaStream_t st) {
   if constexpr (sizeof(T) == 8) {
     if (pre_f) {  // f holds hh*f
+      if (int_adds == kIntAddsAdaptive) return df_column_tile<T, AdaptColumnPre>(ctx, run, tx, ty, any_f, st);
       if (int_adds == 2) return df_column_tile<T, ArithPreF<ArithF64Mix<0x15u>>>(ctx, run, tx, ty, any_f, st);
       if (int_adds == 0) return df_column_tile<T, ArithPreF<ArithF64Fma>>(ctx, run, tx, ty, any_f, st);
-      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "prescaled f with int_adds = %d (0 or 2)", int_adds);
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "prescaled f with int_adds = %d (0, 2 or 6)", int_adds);
     }
+    if (int_adds == kIntAddsAdaptive) return df_column_tile<T, AdaptColumn>(ctx, run, tx, ty, any_f, st);
     if (int_adds == 1) return df_column_tile<T, ArithF64Mix<0x1Du>>(ctx, run, tx, ty, any_f, st);
     if (int_adds == 2) return df_column_tile<T, ArithF64Mix<0x15u>>(ctx, run, tx, ty, any_f, st);
     if (int_adds == 3) return df_column_tile<T, ArithF64Mix<0x12u>>(ctx, run, tx, ty, any_f, st);
@@ -307,6 +318,10 @@ template int gs_column_run<double, ArithF64Mix<0x10u>>(stencil_ctx*, double*, co
                                   int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<double, ArithF64Mix<0x00u>>(stencil_ctx*, double*, const double*, const Geom&, Coef<double>, int, int,
                                   int, int, bool, int, double, cudaStream_t, bool);
+template int gs_column_run<double, AdaptColumn>(stencil_ctx*, double*, const double*, const Geom&,
+                                  Coef<double>, int, int, int, int, bool, int, double, cudaStream_t, bool);
+template int gs_column_run<double, AdaptColumnPre>(stencil_ctx*, double*, const double*, const Geom&,
+                                  Coef<double>, int, int, int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<double, ArithPreF<ArithF64Fma>>(stencil_ctx*, double*, const double*, const Geom&,
                                   Coef<double>, int, int, int, int, bool, int, double, cudaStream_t, bool);
 template int gs_column_run<double, ArithPreF<ArithF64Mix<0x15u>>>(stencil_ctx*, double*, const double*, const Geom&,

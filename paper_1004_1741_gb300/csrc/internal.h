@@ -120,8 +120,16 @@ constexpr int STENCIL_UNSUPPORTED_TILE = 1;
 // 2, 148 at 3, 129 at 4; Gauss-Seidel column march (8x8, persistent) 105 at 2,
 // 103 at 3; Gauss-Seidel tile tasks 66 at 0, 71 at 1, 70.5 at 2
 constexpr int kDefaultIntAdds = 1;
-constexpr int kDefaultIntAddsJacobi = 3;
-constexpr int kDefaultIntAddsColumn = 2;
+// int_adds = 6: the adaptive form (ArithAdaptive): per warp and update, 3 (Jacobi z-march) or 2
+// (column march) integer-pipe additions when the neighbours are non-negative, else the additions on
+// the FP64 pipe and the multiplication on the integer path; the FP64 default of both families
+constexpr int kIntAddsAdaptive = 6;
+constexpr int kDefaultIntAddsJacobi = kIntAddsAdaptive;
+constexpr int kDefaultIntAddsColumn = kIntAddsAdaptive;
+using AdaptJacobi = ArithAdaptive<ArithF64Mix<0x12u>, ArithF64Mix<0x1Fu, true>>;
+using AdaptJacobiPre = ArithAdaptive<ArithPreF<ArithF64Mix<0x12u>>, ArithPreF<ArithF64Mix<0x1Fu, true>>>;
+using AdaptColumn = ArithAdaptive<ArithF64Mix<0x15u>, ArithF64Mix<0x1Fu, true>>;
+using AdaptColumnPre = ArithAdaptive<ArithPreF<ArithF64Mix<0x15u>>, ArithPreF<ArithF64Mix<0x1Fu, true>>>;
 void dataflow_release(stencil_ctx* ctx);  // internal: no kernel instantiated for a tile shape
 
 // Persistent dataflow run of the skewed-tile schedule over n grids (dataflow.cu).

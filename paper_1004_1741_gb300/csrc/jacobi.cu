@@ -102,10 +102,17 @@ struct JacobiLaunch {
                         cudaStream_t st) {
     dim3 block(32, BY);
     dim3 grid((g.nx + 31) / 32, (g.ny + BY - 1) / BY, (g.nz + zchunk - 1) / zchunk);
-    if (pipe)
-      jacobi_pipe_kernel<T, Ar, HAS_F, WEIGHTED, BY, 8><<<grid, block, 0, st>>>(src, dst, f, g, zchunk, c);
-    else
-      jacobi_zmarch_kernel<T, Ar, HAS_F, WEIGHTED, BY><<<grid, block, 0, st>>>(src, dst, f, g, zchunk, c);
+    if constexpr (!AdaptOf<Ar>::on) {  // the copy-ahead variant has no adaptive form (it runs Pos)
+      if (pipe) {
+        jacobi_pipe_kernel<T, Ar, HAS_F, WEIGHTED, BY, 8><<<grid, block, 0, st>>>(src, dst, f, g, zchunk, c);
+        return cudaGetLastError();
+      }
+    } else if (pipe) {
+      jacobi_pipe_kernel<T, typename Ar::Pos, HAS_F, WEIGHTED, BY, 8><<<grid, block, 0, st>>>(src, dst, f, g, zchunk,
+                                                                                               c);
+      return cudaGetLastError();
+    }
+    jacobi_zmarch_kernel<T, Ar, HAS_F, WEIGHTED, BY><<<grid, block, 0, st>>>(src, dst, f, g, zchunk, c);
     return cudaGetLastError();
   }
   template <class Ar, int BY>
@@ -142,6 +149,7 @@ cudaError_t jacobi_sweep(const T* src, T* dst, const T* f, const Geom& g, int by
       case 3: return jacobi_sweep_ar<T, ArithF64Mix<0x12u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
       case 4: return jacobi_sweep_ar<T, ArithF64Mix<0x10u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
       case 5: return jacobi_sweep_ar<T, ArithF64Mix<0x00u>>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
+      case kIntAddsAdaptive: return jacobi_sweep_ar<T, AdaptJacobi>(src, dst, f, g, by, zchunk, c, weighted, pipe, st);
       default: break;
     }
   }
@@ -161,27 +169,29 @@ cudaError_t prescale_f(const double* f, double* g, size_t n, double hh, int sm_c
   return cudaGetLastError();
 }
 
-// One unweighted FP64 z-march sweep whose f holds hh*f already (tile height 4 or 8).
+// One unweighted FP64 z-march sweep whose f holds hh*f already (tile height 4 or 8); Ar is an ArithPreF
+// arithmetic (or an ArithAdaptive of two).
 template <class Ar>
 static cudaError_t jacobi_sweep_pre_ar(const double* src, double* dst, const double* gf, const Geom& g, int by,
                                        int zchunk, Coef<double> c, cudaStream_t st) {
   dim3 grid((g.nx + 31) / 32, (g.ny + by - 1) / by, (g.nz + zchunk - 1) / zchunk);
   if (by == 4)
-    jacobi_zmarch_kernel<double, ArithPreF<Ar>, true, false, 4><<<grid, dim3(32, 4), 0, st>>>(src, dst, gf, g, zchunk, c);
+    jacobi_zmarch_kernel<double, Ar, true, false, 4><<<grid, dim3(32, 4), 0, st>>>(src, dst, gf, g, zchunk, c);
   else
-    jacobi_zmarch_kernel<double, ArithPreF<Ar>, true, false, 8><<<grid, dim3(32, 8), 0, st>>>(src, dst, gf, g, zchunk, c);
+    jacobi_zmarch_kernel<double, Ar, true, false, 8><<<grid, dim3(32, 8), 0, st>>>(src, dst, gf, g, zchunk, c);
   return cudaGetLastError();
 }
 
 static cudaError_t jacobi_sweep_pre(const double* src, double* dst, const double* gf, const Geom& g, int by,
                                     int zchunk, Coef<double> c, int int_adds, cudaStream_t st) {
   switch (int_adds) {
-    case 1: return jacobi_sweep_pre_ar<ArithF64Mix<0x1Du>>(src, dst, gf, g, by, zchunk, c, st);
-    case 2: return jacobi_sweep_pre_ar<ArithF64Mix<0x15u>>(src, dst, gf, g, by, zchunk, c, st);
-    case 3: return jacobi_sweep_pre_ar<ArithF64Mix<0x12u>>(src, dst, gf, g, by, zchunk, c, st);
-    case 4: return jacobi_sweep_pre_ar<ArithF64Mix<0x10u>>(src, dst, gf, g, by, zchunk, c, st);
-    case 5: return jacobi_sweep_pre_ar<ArithF64Mix<0x00u>>(src, dst, gf, g, by, zchunk, c, st);
-    default: return jacobi_sweep_pre_ar<ArithF64Fma>(src, dst, gf, g, by, zchunk, c, st);
+    case 1: return jacobi_sweep_pre_ar<ArithPreF<ArithF64Mix<0x1Du>>>(src, dst, gf, g, by, zchunk, c, st);
+    case 2: return jacobi_sweep_pre_ar<ArithPreF<ArithF64Mix<0x15u>>>(src, dst, gf, g, by, zchunk, c, st);
+    case 3: return jacobi_sweep_pre_ar<ArithPreF<ArithF64Mix<0x12u>>>(src, dst, gf, g, by, zchunk, c, st);
+    case 4: return jacobi_sweep_pre_ar<ArithPreF<ArithF64Mix<0x10u>>>(src, dst, gf, g, by, zchunk, c, st);
+    case 5: return jacobi_sweep_pre_ar<ArithPreF<ArithF64Mix<0x00u>>>(src, dst, gf, g, by, zchunk, c, st);
+    case kIntAddsAdaptive: return jacobi_sweep_pre_ar<AdaptJacobiPre>(src, dst, gf, g, by, zchunk, c, st);
+    default: return jacobi_sweep_pre_ar<ArithPreF<ArithF64Fma>>(src, dst, gf, g, by, zchunk, c, st);
   }
 }
 
@@ -277,8 +287,8 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
   if (variant < 0 || variant > 4) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
   const bool pipe = variant == 2;
   const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsJacobi;
-  if (int_adds < 0 || int_adds > 5)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
+  if (int_adds < 0 || int_adds > kIntAddsAdaptive)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..6)", int_adds);
   Coef<T> c = make_coef<T>(h, p);
   int by = (p && p->tile_y) ? p->tile_y : (sizeof(T) == 8 ? 4 : 8);  // FP64: 32x4 measured fastest
   if (by != 4 && by != 8 && by != 16)

@@ -83,6 +83,8 @@ static cudaError_t slab_step(int int_adds, int by, const T* src, T* dst, const T
       case 3: return slab_by<T, ArithF64Mix<0x12u>>(by, src, dst, f, gs, c, weighted, u, cb, cb_k0, cb_planes, st);
       case 4: return slab_by<T, ArithF64Mix<0x10u>>(by, src, dst, f, gs, c, weighted, u, cb, cb_k0, cb_planes, st);
       case 5: return slab_by<T, ArithF64Mix<0x00u>>(by, src, dst, f, gs, c, weighted, u, cb, cb_k0, cb_planes, st);
+      case kIntAddsAdaptive:
+        return slab_by<T, AdaptJacobi>(by, src, dst, f, gs, c, weighted, u, cb, cb_k0, cb_planes, st);
       default: break;
     }
   }
@@ -100,8 +102,8 @@ int jacobi_inplace_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double
   if (p && p->tile_x && p->tile_x != 32)
     return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "Jacobi tile_x = %d (supported 32)", p->tile_x);
   const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsJacobi;
-  if (int_adds < 0 || int_adds > 5)
-    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..5)", int_adds);
+  if (int_adds < 0 || int_adds > kIntAddsAdaptive)
+    return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..6)", int_adds);
   int status = STENCIL_OK;
   const size_t slab_elems = (size_t)S * (size_t)g.sy;
   T* ring = (T*)ws_get(ctx, SLOT_JACOBI_SLABS, 3 * slab_elems * sizeof(T), &status);

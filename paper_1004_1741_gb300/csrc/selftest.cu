@@ -1,6 +1,6 @@
 // Self-check of the integer-pipe binary64 additions (common.cuh int_add_f64 and
-// its ordered form int_add_f64_ge) against the FP64 pipe on generated operand
-// pairs.
+// its ordered form int_add_f64_ge) and of the integer-arithmetic multiplication
+// (int_mul_f64) against the FP64 pipe on generated operand pairs.
 #include "internal.h"
 
 namespace stn {
@@ -54,6 +54,10 @@ __global__ void selftest_int_add_kernel(unsigned long long n, unsigned long long
     // the ordered form, in both argument orders
     if (int_add_f64_ge(a, b, &em) && __double_as_longlong(em) != __double_as_longlong(ref)) ++mism;
     if (int_add_f64_ge(b, a, &em) && __double_as_longlong(em) != __double_as_longlong(__dadd_rn(b, a))) ++mism;
+    // the integer-path multiplication, on the same pair with independent random signs
+    const double sa = ((r3 >> 17) & 1ull) ? -a : a, sb = ((r3 >> 18) & 1ull) ? -b : b;
+    if (int_mul_f64(sa, sb, &em) && __double_as_longlong(em) != __double_as_longlong(__dmul_rn(sa, sb))) ++mism;
+    if (int_mul_f64(sb, sa, &em) && __double_as_longlong(em) != __double_as_longlong(__dmul_rn(sb, sa))) ++mism;
   }
   atomicAdd(counts, mism);
   atomicAdd(counts + 1, fast);

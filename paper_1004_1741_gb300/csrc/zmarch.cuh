@@ -56,9 +56,15 @@ __device__ __forceinline__ void zmarch_body(const T* __restrict__ src, T* __rest
     T fv = T(0);
     if (HAS_F && active) fv = *pf;
     __syncthreads();
-    if (active)
+    if constexpr (AdaptOf<Ar>::on) {  // the whole warp votes (its lanes are converged here)
+      const T v = site_update_warp<T, Ar, HAS_F, WEIGHTED>(active, sm[bf][ty + 1][tx], sm[bf][ty + 1][tx + 2],
+                                                           sm[bf][ty][tx + 1], sm[bf][ty + 2][tx + 1], below,
+                                                           above, fv, cur, c);
+      if (active) *pd = v;
+    } else if (active) {
       *pd = site_update<T, Ar, HAS_F, WEIGHTED>(sm[bf][ty + 1][tx], sm[bf][ty + 1][tx + 2], sm[bf][ty][tx + 1],
                                                 sm[bf][ty + 2][tx + 1], below, above, fv, cur, c);
+    }
     below = cur;
     cur = above;
     above = next;

@@ -336,6 +336,49 @@ def test_prescaled_f_and_budget_fallback(case):
     assert launches[0] - launches[1] == (1 if prescaled else 0), launches
 
 
+def _two_sign_grid(dims, seed, with_f):
+    """Upper half of the planes negative, lower half positive: warps of one launch take both branches of
+    the adaptive arithmetic (and the planes between take mixed neighbourhoods)."""
+    u0, f0 = W.random_grid(*dims, seed=seed, with_f=with_f)
+    u0 = u0.copy()
+    u0[u0.shape[0] // 2:] *= -1.0
+    return u0, f0
+
+
+@pytest.mark.parametrize("with_f", [False, True])
+@pytest.mark.parametrize("case", [("jacobi", 0), ("jacobi", 6), ("gs", 4), ("gs", 5)])
+def test_adaptive_arithmetic_both_signs(ctx, case, with_f):
+    """int_adds = 6 (the FP64 default of the z-march and the column march): per warp and update the
+    integer-pipe additions for non-negative neighbourhoods, else FP64-pipe additions and the integer-path
+    multiplication; the oracle's bits either way."""
+    smoother, variant = case
+    dims = (70, 21, 30)
+    u0, f0 = _two_sign_grid(dims, 31, with_f)
+    fn, ofn = (capi.stencil_jacobi, oracle.jacobi) if smoother == "jacobi" else (capi.stencil_gs_lex, oracle.gs_lex)
+    ref = ofn(u0, f0, 0.02, 5)
+    for ia in (-1, 6):
+        _assert_exact(_run(ctx, fn, u0, f0, 0.02, 5, variant=variant, int_adds=ia), ref,
+                      "%s variant %d int_adds %d" % (smoother, variant, ia))
+    # weighted Jacobi takes the adaptive z-march too
+    if smoother == "jacobi" and variant == 0:
+        ref_w = oracle.jacobi(u0, f0, 0.02, 3, a=0.25, b=0.125)
+        _assert_exact(_run(ctx, fn, u0, f0, 0.02, 3, a=0.25, b=0.125), ref_w, "weighted adaptive")
+
+
+def test_batched_adaptive_both_signs(ctx):
+    dims = [(40, 12, 9), (33, 9, 16), (9, 33, 7)]
+    grids = [_two_sign_grid(d, 70 + i, i != 1) for i, d in enumerate(dims)]
+    hs = [W.grid_h(*d) for d in dims]
+    sweeps = [4, 3, 6]
+    for sm, ofn in ((capi.STENCIL_JACOBI, oracle.jacobi), (capi.STENCIL_GS, oracle.gs_lex)):
+        us = [_dev(u) for u, _ in grids]
+        fs = [_dev(f) for _, f in grids]
+        capi.stencil_batched(ctx, us, fs, hs, sweeps, sm, int_adds=6)
+        torch.cuda.synchronize()
+        for i, ((u0, f0), h, ns) in enumerate(zip(grids, hs, sweeps)):
+            _assert_exact(us[i].cpu().numpy(), ofn(u0, f0, h, ns), "batched adaptive %d grid %d" % (sm, i))
+
+
 def test_batched_prescaled_f(ctx):
     """Batched FP64 Poisson grids (Jacobi z-march and Gauss-Seidel column tasks) with prescaled f, grids with
     and without f and one-sweep grids in the mix."""
@@ -476,7 +519,8 @@ def test_full_size_400_bench_config(ctx, smoother):
     with cf.ThreadPoolExecutor(1) as ex:  # the oracle releases the GIL inside C
         fut = ex.submit(oracle.jacobi if smoother == "jacobi" else oracle.gs_lex, u0, None, 1.0, 100)
         fn = capi.stencil_jacobi if smoother == "jacobi" else capi.stencil_gs_lex
-        got = _run(ctx, fn, u0, None, 1.0, 100, nt=cfg["nt"], tile=cfg["tile"], variant=cfg["variant"])
+        got = _run(ctx, fn, u0, None, 1.0, 100, nt=cfg["nt"], tile=cfg["tile"], variant=cfg["variant"],
+                   int_adds=cfg["int_adds"])
         ref = fut.result()
     _assert_exact(got, ref, "400^3 %s" % smoother)
 
