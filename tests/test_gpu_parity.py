@@ -281,9 +281,10 @@ def test_batched_uneven_grids(ctx, smoother, dtype, nt):
         _assert_exact(us[i].cpu().numpy(), ofn(u0, f0, h, ns), "batched grid %d" % i)
 
 
+@pytest.mark.parametrize("tile", [(0, 0, 0), (0, 8, 40), (32, 4, 7)])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 @pytest.mark.parametrize("int_adds", [-1, 0, 5])
-def test_batched_jacobi_zmarch_many_grids(ctx, dtype, int_adds):
+def test_batched_jacobi_zmarch_many_grids(ctx, dtype, int_adds, tile):
     """Jacobi at nt = 1: one launch per sweep over every grid's tile columns; grids of ragged x/y tiles, a
     column taller than one z-chunk (300 planes), grids that stop early and grids with and without f."""
     dims = [(33, 5, 7), (1, 1, 300), (40, 9, 3), (31, 4, 1), (65, 13, 2)] + [(8 + i, 3 + i % 5, 2 + i % 7)
@@ -293,7 +294,7 @@ def test_batched_jacobi_zmarch_many_grids(ctx, dtype, int_adds):
     sweeps = [(3 * i) % 8 for i in range(len(dims))]
     us = [_dev(u) for u, _ in grids]
     fs = [_dev(f) for _, f in grids]
-    capi.stencil_batched(ctx, us, fs, hs, sweeps, capi.STENCIL_JACOBI, int_adds=int_adds)
+    capi.stencil_batched(ctx, us, fs, hs, sweeps, capi.STENCIL_JACOBI, int_adds=int_adds, tile=tile)
     torch.cuda.synchronize()
     for i, ((u0, f0), h, ns) in enumerate(zip(grids, hs, sweeps)):
         _assert_exact(us[i].cpu().numpy(), oracle.jacobi(u0, f0, h, ns), "batched Jacobi grid %d" % i)
@@ -363,6 +364,15 @@ def test_adaptive_arithmetic_both_signs(ctx, case, with_f):
     if smoother == "jacobi" and variant == 0:
         ref_w = oracle.jacobi(u0, f0, 0.02, 3, a=0.25, b=0.125)
         _assert_exact(_run(ctx, fn, u0, f0, 0.02, 3, a=0.25, b=0.125), ref_w, "weighted adaptive")
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_adaptive_value_on_gs_tile_paths(ctx, variant):
+    """int_adds = 6 on the Gauss-Seidel tile paths (nt = 2) runs their own default and gives the oracle's bits."""
+    u0, f0 = _two_sign_grid((29, 17, 21), 41, True)
+    ref = oracle.gs_lex(u0, f0, 0.05, 4)
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.05, 4, nt=2, tile=(16, 16, 16), variant=variant,
+                       int_adds=6), ref, "gs tiles variant %d" % variant)
 
 
 def test_batched_adaptive_both_signs(ctx):
