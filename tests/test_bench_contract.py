@@ -1,0 +1,43 @@
+"""bench.py's reference arm (the serial oracle on the host cores) and the shape of its JSON line.
+
+Runs without a GPU: the reference arm times the oracle only.
+"""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["value"] > 0 and d["unit"] == "GLUP/s" and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
+    assert "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_headline_names_every_launch_parameter():
+    """The headline's launch configuration (timed by bench.py and checked at full size by the GPU
+    parity tests) names every tuning parameter it depends on."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for name in ("jacobi", "gs"):
+        cfg = bench.HEADLINE[name]
+        assert set(cfg) == {"nt", "tile", "variant", "int_adds"}
+        assert cfg["nt"] == 1 and 0 <= cfg["int_adds"] <= 6
