@@ -96,7 +96,9 @@ size_t stencil_workspace_bytes(const stencil_ctx* ctx);
  * benchmarks: every kernel launch of every entry point adds one). */
 unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
 
-/* Tuning of one smoother call (all fields 0 = library default).
+/* Tuning of one smoother call (fields 0 = library default, except int_adds,
+ * where 0 puts every addition on the FP64 pipe and -1 is the default: set it
+ * to -1 in a zero-initialised struct).
  *  nt      sweeps applied per pass over device memory (temporal blocking,
  *          Sec. 4); 1 = one sweep per pass.  Range 1..16.
  *  tile_x, tile_y, tile_z
@@ -257,9 +259,11 @@ int stencil_mg_solve(stencil_ctx* ctx, double* u, const double* f, const int64_t
 int stencil_set_wait_limit(stencil_ctx* ctx, long long timeout_ns, long long never_publish);
 
 /* Autotuner (not in the paper): times candidate kernel variants, temporal
- * depths nt and tiles for `smoother` on a copy of the caller's grid u (device,
- * dtype STENCIL_F64/F32; f may be NULL) for nsweeps sweeps and writes the
- * fastest into *out (and its GLUP/s into *out_glups if not NULL).  u is not
+ * depths nt, tiles and (FP64, one sweep per pass) the integer-pipe form --
+ * the adaptive default or the fixed form fastest on non-negative data -- for
+ * `smoother` on a copy of the caller's grid u (device, dtype STENCIL_F64/F32;
+ * f may be NULL) for nsweeps sweeps and writes the fastest, int_adds
+ * included, into *out (and its GLUP/s into *out_glups if not NULL).  u is not
  * modified.  Blocking. */
 int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, const void* f, const int64_t dims[3],
                      double h, int nsweeps, stencil_params* out, double* out_glups, void* stream);

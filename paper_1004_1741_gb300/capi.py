@@ -332,7 +332,8 @@ def stencil_autotune(ctx: Context, smoother: int, u: torch.Tensor, f: torch.Tens
     rc = lib.stencil_autotune(ctx.handle, int(smoother), dtype, _grid(u, u.dtype), _opt_grid(f, u, u.dtype), _dims(u),
                               float(h), int(nsweeps), ctypes.byref(out), ctypes.byref(g), _stream(stream))
     _check(ctx, rc)
-    return ({"nt": out.nt, "tile": (out.tile_x, out.tile_y, out.tile_z), "variant": out.variant}, g.value)
+    return ({"nt": out.nt, "tile": (out.tile_x, out.tile_y, out.tile_z), "variant": out.variant,
+             "int_adds": out.int_adds}, g.value)
 
 
 def residual_norm_noalloc(u: torch.Tensor, f: torch.Tensor | None, h: float, r_out: torch.Tensor | None = None,

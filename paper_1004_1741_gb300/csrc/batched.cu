@@ -160,27 +160,38 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
   cudaStream_t st = (cudaStream_t)stream;
   const size_t esz = dtype == STENCIL_F64 ? 8 : 4;
   const size_t bytes = (size_t)g.sy * (size_t)(g.nz + 2) * esz;
-  // candidates: (variant, nt, tile); the caller's grid is copied, never modified
+  // candidates: (variant, nt, tile, int_adds); the caller's grid is copied, never modified.  int_adds -1 is
+  // each path's default (the adaptive form on the z-march and the column march); FP64 also tries the fixed
+  // forms those two are fastest with on non-negative data (3 and 2 integer-pipe additions)
   struct Cand {
-    int variant, nt, tx, ty, tz;
+    int variant, nt, tx, ty, tz, int_adds;
   };
+  const bool f64 = dtype == STENCIL_F64;
   std::vector<Cand> cands;
   if (smoother == STENCIL_GS) {
-    cands.push_back({4, 1, 0, 0, 0});  // column march, per-dtype default tile
-    for (int ty : {8, 16}) cands.push_back({4, 1, 8, ty, 0});
-    cands.push_back({4, 1, 16, 8, 0});
+    for (int ia : {-1, 2}) {
+      if (ia >= 0 && !f64) continue;
+      cands.push_back({4, 1, 0, 0, 0, ia});  // column march, per-dtype default tile
+      for (int ty : {8, 16}) cands.push_back({4, 1, 8, ty, 0, ia});
+      cands.push_back({4, 1, 16, 8, 0, ia});
+      cands.push_back({5, 1, 0, 0, 0, ia});  // the same as one persistent launch
+    }
     const int nts[] = {1, 2, 4, 8};
     const int tiles[][3] = {{16, 16, 16}, {32, 8, 8}, {32, 16, 16}};
     for (int v : {0, 3})
       for (int nt : nts)
         for (auto& t : tiles)
-          if (nt <= t[1] && nt <= t[2] && (dtype == STENCIL_F32 || nt <= 8)) cands.push_back({v, nt, t[0], t[1], t[2]});
+          if (nt <= t[1] && nt <= t[2] && (dtype == STENCIL_F32 || nt <= 8))
+            cands.push_back({v, nt, t[0], t[1], t[2], -1});
   } else {
-    for (int by : {4, 8, 16}) cands.push_back({0, 1, 32, by, 0});
+    for (int ia : {-1, 3}) {
+      if (ia >= 0 && !f64) continue;
+      for (int by : {4, 8, 16}) cands.push_back({0, 1, 32, by, 0, ia});
+    }
     const int nts[] = {2, 4, 8};
     const int tiles[][3] = {{32, 8, 8}, {32, 16, 8}, {32, 16, 16}};
     for (int nt : nts)
-      for (auto& t : tiles) cands.push_back({0, nt, t[0], t[1], t[2]});
+      for (auto& t : tiles) cands.push_back({0, nt, t[0], t[1], t[2], -1});
   }
   int status;
   void* scratch = ws_get(ctx, SLOT_TUNE_GRID, bytes, &status);
@@ -200,6 +211,7 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
     q.tile_y = c.ty;
     q.tile_z = c.tz;
     q.variant = c.variant;
+    q.int_adds = c.int_adds;
     e = cudaMemcpyAsync(scratch, u, bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) break;
     auto run = [&]() -> int {
@@ -232,6 +244,7 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
   out->tile_y = bestc.ty;
   out->tile_z = bestc.tz;
   out->variant = bestc.variant;
+  out->int_adds = bestc.int_adds;
   if (out_glups) *out_glups = best;
   return STENCIL_OK;
 }
