@@ -210,19 +210,21 @@ int residual_norm(stencil_ctx* ctx, const double* u, const double* f, const int6
  * persistent kernel launch replayed from a CUDA graph (the tasks of all grids
  * share one dependency-ordered work queue, so small grids fill the GPU
  * together); Jacobi at nt = 1 (variant 0) runs one z-march launch per sweep
- * over the tile columns of every grid that still has sweeps to do.  u[i], f[i]: device pointers of grid i (f may be NULL,
- * or f[i] NULL, for f = 0); dims[3i..3i+2] its interior extents; h[i],
- * nsweeps[i] (host arrays).  smoother: STENCIL_JACOBI or STENCIL_GS; dtype:
- * STENCIL_F64 or STENCIL_F32 (u and f are double* or float* accordingly).
- * Every grid ends exactly as after stencil_jacobi / stencil_gs_lex with the
- * same arguments.  params (may be NULL): nt, tile, b and int_adds shared by
- * all grids (defaults nt = 1; Gauss-Seidel at nt = 1: column-march tasks of
- * 8x8 columns (16x8 for FP32) x 100 planes unless variant is 1..3, else
- * 16^3 tile tasks; Jacobi 32x4 (FP64) or 32x8 (FP32) z-march columns at
- * nt = 1, else 32x8x8 tile tasks); a must be 0.  Jacobi takes a
- * workspace of the total size of the batch.  Blocking: returns when the batch
- * is done; STENCIL_ERR_TIMEOUT if a bounded device wait expired (the grids
- * are then undefined, the context stays usable). */
+ * over the tile columns of every grid that still has sweeps to do.
+ * u[i], f[i]: device pointers of grid i (f may be NULL, or f[i] NULL, for
+ * f = 0); dims[3i..3i+2] its interior extents; h[i], nsweeps[i] (host
+ * arrays).  smoother: STENCIL_JACOBI or STENCIL_GS; dtype: STENCIL_F64 or
+ * STENCIL_F32 (u and f are double* or float* accordingly).  Every grid ends
+ * exactly as after stencil_jacobi / stencil_gs_lex with the same arguments.
+ * params (may be NULL): nt, tile, b and int_adds shared by all grids
+ * (defaults nt = 1; Gauss-Seidel at nt = 1: column-march tasks of 8x8
+ * columns (16x8 for FP32) x 100 planes unless variant is 1..3, else 16^3
+ * tile tasks; Jacobi 32x4 (FP64) or 32x8 (FP32) z-march columns at nt = 1,
+ * else 32x8x8 tile tasks; FP64 int_adds: the adaptive form); a must be 0.
+ * Jacobi takes a workspace of the total size of the batch, FP64 with f a
+ * further one for h^2 f when the budget has room.  Blocking: returns when the
+ * batch is done; STENCIL_ERR_TIMEOUT if a bounded device wait expired (the
+ * grids are then undefined, the context stays usable). */
 int stencil_batched(stencil_ctx* ctx, int n, void* const* u, const void* const* f, const int64_t* dims,
                     const double* h, const int* nsweeps, int smoother, int dtype, const stencil_params* params,
                     void* stream);
