@@ -139,6 +139,33 @@ def test_gs_red_black_f32_matches_f64_within_single_precision():
     np.testing.assert_allclose(out32.astype(np.float64), out64, rtol=0, atol=64 * EPS32)
 
 
+@pytest.mark.parametrize("smoother", ["jacobi", "gs_lex"])
+@pytest.mark.parametrize("with_f", [False, True])
+def test_f32_error_against_f64_within_the_rounding_bound(smoother, with_f):
+    """FP32 sweeps against FP64 sweeps from the same (FP32-representable) data: one sweep rounds the
+    partial sums of the neighbour sum (at most 2..6 max|u|) to 2^-24 relative, 20 units of
+    2^-24 max|u| times b = 1/6, plus the multiplication: 4.34 units; with f the bracket's last
+    addition and h^2 f add (2 h^2 max|f| / 6 + ...) units.  Both smoothers are convex combinations
+    of their neighbours (weights 1/6), so an error's max-norm never grows: after n sweeps
+    |u32 - u64| <= n (4.34 max|u| + h^2 max|f|) 2^-24.  A wrong FP32 constant or operation
+    breaks it by orders of magnitude."""
+    nx, ny, nz = 30, 21, 17
+    rng = np.random.default_rng(12)
+    u = rng.random((nz + 2, ny + 2, nx + 2)).astype(np.float32)
+    f = rng.standard_normal(u.shape).astype(np.float32) if with_f else None
+    h = 1.0 / 31
+    fn = oracle.jacobi if smoother == "jacobi" else oracle.gs_lex
+    for n in (1, 10, 60):
+        out32 = fn(u, f, h, n)
+        out64 = fn(u.astype(np.float64), None if f is None else f.astype(np.float64), h, n)
+        umax = max(np.abs(out64).max(), np.abs(u).max())
+        hf = np.float32(h * h) * np.abs(f).max() if with_f else 0.0
+        bound = n * (4.34 * umax + hf) * 2.0 ** -24
+        err = np.abs(out32.astype(np.float64) - out64).max()
+        assert err <= bound, (smoother, with_f, n, err, bound)
+        assert err > 0 or n == 0  # FP32 really rounds differently
+
+
 # ------------------------------------------------- schedules (exactness) ----
 @pytest.mark.parametrize("dims", [(4, 4, 4), (5, 3, 6), (1, 1, 5), (6, 2, 1)])
 def test_gs_hyperplane_order_is_bit_exact(dims):
