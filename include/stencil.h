@@ -64,7 +64,7 @@ extern "C" {
 #define STENCIL_ERR_CUDA (-3)          /* a CUDA runtime call or kernel launch failed       */
 #define STENCIL_ERR_TIMEOUT (-4)       /* a bounded device-side wait expired                */
 #define STENCIL_ERR_NOT_CONVERGED (-5) /* a solve stopped at its cap; outputs still valid   */
-#define STENCIL_ERR_UNSUPPORTED (-6)   /* valid request this build does not implement      */
+#define STENCIL_ERR_UNSUPPORTED (-6)   /* valid request the library does not implement     */
 #define STENCIL_ERR_CANCELLED (-7)     /* a served request was cancelled before admission   */
 
 #define STENCIL_JACOBI 0
