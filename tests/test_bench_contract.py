@@ -41,3 +41,35 @@ def test_headline_names_every_launch_parameter():
         cfg = bench.HEADLINE[name]
         assert set(cfg) == {"nt", "tile", "variant", "int_adds"}
         assert cfg["nt"] == 1 and 0 <= cfg["int_adds"] <= 6
+
+
+def test_traffic_record_is_used_only_for_the_measured_source(tmp_path, monkeypatch):
+    """roofline.traffic comes from profiles/dram_traffic.txt only while the kernel's source file still
+    hashes to the value recorded with the counters; any edit turns it into null."""
+    import hashlib
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "dram_traffic.txt").write_text("# comment\nk_kernel k.cu %s 123456\n" % digest)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic_from_profiles("k_kernel") == 123456.0
+    assert bench._traffic_from_profiles("other_kernel") is None
+    src.write_text("__global__ void k() { }\n")
+    assert bench._traffic_from_profiles("k_kernel") is None
+
+
+def test_committed_traffic_records_name_existing_sources():
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    for ln in open(path):
+        ln = ln.strip()
+        if not ln or ln.startswith("#"):
+            continue
+        kernel, src, digest, value = ln.split()[:4]
+        assert os.path.exists(os.path.join(ROOT, src)), src
+        assert len(digest) == 16 and float(value) > 0, ln
+
