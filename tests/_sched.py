@@ -207,6 +207,53 @@ def jacobi_wavefront_paper(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int =
     return src
 
 
+def jacobi_slab_ring(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int = 1, slab: int = 2,
+                     copy_first: bool = False, lag: int = 2) -> np.ndarray:
+    """Jacobi in place through a ring of three z-slab buffers (the GPU's variant 6): slab s (planes
+    [s*slab, (s+1)*slab)) is computed from ``src`` into buffer s % 3, and the same launch copies
+    slab s - lag back from its buffer into ``src``; the last slabs still in the ring are copied back
+    at the end of the sweep.  The copy-back and the computation of one launch may interleave in
+    any way on the GPU; ``copy_first`` runs the copy before the computation (the other extreme), and
+    both orders must give the serial result.  ``lag`` is 2 in the library."""
+    src = u.copy()
+    nz, ny, nx = (d - 2 for d in u.shape)
+    b, hh = _consts(u, h)
+    nslab = (nz + slab - 1) // slab
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    J, I = jj + 1, ii + 1
+    buf = [np.zeros((slab, ny, nx), dtype=u.dtype) for _ in range(3)]
+
+    def planes(s):
+        return range(s * slab, min(nz, (s + 1) * slab))
+
+    def compute(s):
+        for q, p in enumerate(planes(s)):
+            z = p + 1
+            acc = src[z, J, I - 1] + src[z, J, I + 1]
+            acc = acc + src[z, J - 1, I]
+            acc = acc + src[z, J + 1, I]
+            acc = acc + src[z - 1, J, I]
+            acc = acc + src[z + 1, J, I]
+            if f is not None:
+                acc = acc + hh * f[z, J, I]
+            buf[s % 3][q] = b * acc
+
+    def copy_back(s):
+        for q, p in enumerate(planes(s)):
+            src[p + 1, J, I] = buf[s % 3][q]
+
+    for _ in range(nsweeps):
+        for s in range(nslab):
+            if s >= lag and copy_first:
+                copy_back(s - lag)
+            compute(s)
+            if s >= lag and not copy_first:
+                copy_back(s - lag)
+        for s in range(max(0, nslab - lag), nslab):
+            copy_back(s)
+    return src
+
+
 def jacobi_skewed_tiles(u: np.ndarray, f=None, h: float = 1.0, nsweeps: int = 1, tile=(4, 4, 4),
                         nt: int = 1, reverse_within_level: bool = False) -> np.ndarray:
     """Jacobi by skewed tiles: the tasks and levels of skewed_tile_tasks, with two

@@ -167,6 +167,27 @@ def test_f32_error_against_f64_within_the_rounding_bound(smoother, with_f):
 
 
 # ------------------------------------------------- schedules (exactness) ----
+@pytest.mark.parametrize("nz", [1, 2, 5, 7, 12])
+@pytest.mark.parametrize("slab", [1, 2, 3, 5, 32])
+@pytest.mark.parametrize("copy_first", [False, True])
+def test_jacobi_slab_ring_is_bit_exact(nz, slab, copy_first):
+    """The GPU's in-place Jacobi (three slab buffers, copy-back two slabs behind, in either order
+    against the computation of the same launch) gives the serial iterate."""
+    rng = np.random.default_rng(nz * 7 + slab)
+    u = rng.random((nz + 2, 6, 5))
+    f = rng.standard_normal(u.shape)
+    for ns in (1, 3):
+        np.testing.assert_array_equal(S.jacobi_slab_ring(u, f, 0.3, ns, slab, copy_first), oracle.jacobi(u, f, 0.3, ns))
+
+
+def test_jacobi_slab_ring_lag_one_breaks():
+    """Copying back the slab just before the one being computed overwrites planes it still reads."""
+    rng = np.random.default_rng(5)
+    u = rng.random((12, 6, 5))
+    got = S.jacobi_slab_ring(u, None, 1.0, 1, slab=2, copy_first=True, lag=1)
+    assert not np.array_equal(got, oracle.jacobi(u, None, 1.0, 1))
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4), (5, 3, 6), (1, 1, 5), (6, 2, 1)])
 def test_gs_hyperplane_order_is_bit_exact(dims):
     """Sites with equal i+j+k+2t are independent: updating them level by level
