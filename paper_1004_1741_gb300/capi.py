@@ -233,7 +233,9 @@ class Context:
 def stencil_jacobi(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int, *, nt: int = 0,
                    tile=(0, 0, 0), a: float = 0.0, b: float = 0.0, variant: int = 0, int_adds: int = -1,
                    stream=None) -> None:
-    """Jacobi sweeps in place on u (FP64 or FP32 by u's dtype)."""
+    """Jacobi sweeps in place on u (FP64 or FP32 by u's dtype).  The keywords are the fields of
+    ``stencil_params`` (include/stencil.h): nt sweeps per pass, tile, weights a and b (0: 1/6),
+    kernel variant, and int_adds (-1: the library default, for FP64 the adaptive integer-pipe form)."""
     lib = load_library()
     p = _params(nt, tile, a, b, variant, int_adds)
     if u.dtype == torch.float64:
@@ -247,7 +249,8 @@ def stencil_jacobi(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: flo
 
 def stencil_gs_lex(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, nsweeps: int, *, nt: int = 0,
                    tile=(0, 0, 0), variant: int = 0, int_adds: int = -1, stream=None) -> None:
-    """Lexicographic Gauss-Seidel sweeps in place on u (FP64 or FP32 by u's dtype)."""
+    """Lexicographic Gauss-Seidel sweeps in place on u (FP64 or FP32 by u's dtype).  The keywords
+    are the fields of ``stencil_params`` (include/stencil.h); int_adds -1 is the library default."""
     lib = load_library()
     p = _params(nt, tile, variant=variant, int_adds=int_adds)
     if u.dtype == torch.float64:
