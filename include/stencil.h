@@ -86,7 +86,8 @@ int stencil_create(stencil_ctx** out, int device, size_t hbm_budget_bytes);
 void stencil_destroy(stencil_ctx* ctx);
 
 /* Text of the last error on this context; never NULL; valid until the next
- * call on the context.  With ctx == NULL, the last error of stencil_create. */
+ * call on the context.  With ctx == NULL, the last error of stencil_create
+ * or residual_norm_noalloc on the calling thread. */
 const char* stencil_last_error(const stencil_ctx* ctx);
 
 /* Bytes the context currently holds on the device. */
@@ -350,19 +351,20 @@ int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t seed, uint64
  * need a residual (an application that owns all device memory through its
  * own allocator, a time-critical loop that must not stall or fragment the
  * heap, code about to be recorded into a CUDA graph).  Same arguments,
- * results and reduction order as residual_norm, but no context: the work
- * runs on the calling thread's current CUDA device, and u, f, r_out must
- * live there.  The reduction scratch is a fixed array inside the library
- * (512 KiB + 16 B on every device that loads it, held until the process
- * exits), so the grid must satisfy
+ * results and reduction order as residual_norm (the same kernels), but no
+ * context: the work runs on the calling thread's current CUDA device, and u,
+ * f and r_out must be device (or managed) memory of that device; anything
+ * else (a host pointer, another device's memory) returns STENCIL_ERR_ARG
+ * before any kernel is launched.  The reduction scratch is a fixed array
+ * inside the library (512 KiB + 16 B on every device that loads it, held
+ * until the process exits), so the grid must satisfy
  *     ceil(nx/32) * ceil(ny/8) * ceil(nz/32) <= 32768
  * (e.g. up to 640^3); larger grids return STENCIL_ERR_ARG with the limit in
- * stencil_last_error(NULL).  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  Every
- * call reuses the same array: calls that overlap on the GPU (two streams,
- * two host threads on one device) race and must be serialised by the
- * caller.  Blocking: synchronises `stream`.  Errors are reported through
- * stencil_last_error(NULL). */
+ * stencil_last_error(NULL).  Each call looks up the array's address in the
+ * current context.  Every call reuses the same array: calls that overlap on
+ * the GPU (two streams, two host threads on one device) race and must be
+ * serialised by the caller.  Blocking: synchronises `stream`.  Errors are
+ * reported through stencil_last_error(NULL), which each call clears first. */
 int residual_norm_noalloc(const double* u, const double* f, const int64_t dims[3], double h, double* r_out,
                           double* out_abs, double* out_rel, void* stream);
 

@@ -342,13 +342,16 @@ def stencil_autotune(ctx: Context, smoother: int, u: torch.Tensor, f: torch.Tens
 def residual_norm_noalloc(u: torch.Tensor, f: torch.Tensor | None, h: float, r_out: torch.Tensor | None = None,
                           stream=None):
     """residual_norm for callers that cannot allocate device memory: no context,
-    a fixed scratch array inside the library, the current CUDA device.  Returns
+    a fixed scratch array inside the library.  Runs on u's device (made current
+    for the call) and, by default, on that device's current stream.  Returns
     (||r||_2, ||r||_2/||f||_2)."""
     lib = load_library()
     ab, rel = ctypes.c_double(0.0), ctypes.c_double(0.0)
-    rc = lib.residual_norm_noalloc(_grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u), float(h),
-                                   _opt_grid(r_out, u, torch.float64), ctypes.byref(ab), ctypes.byref(rel),
-                                   _stream(stream))
+    pu = _grid(u, torch.float64)
+    with torch.cuda.device(u.device):
+        st = _stream(stream if stream is not None else torch.cuda.current_stream(u.device))
+        rc = lib.residual_norm_noalloc(pu, _opt_grid(f, u, torch.float64), _dims(u), float(h),
+                                       _opt_grid(r_out, u, torch.float64), ctypes.byref(ab), ctypes.byref(rel), st)
     _check(None, rc)
     return ab.value, rel.value
 
