@@ -255,6 +255,27 @@ int stencil_mg_solve(stencil_ctx* ctx, double* u, const double* f, const int64_t
                      int nu1, int nu2, int ncoarse, int max_levels, double rtol, int max_cycles, double* out_rel,
                      int* out_cycles, void* stream);
 
+/* Mixed-precision multigrid solve of -Lap_h u = f (not in the paper: the
+ * smoothers of Sec. 3 inside the multigrid solver Sec. 1 and Sec. 3 name,
+ * with the bulk of the work on binary32 storage).  Defect correction:
+ *   r = f - A u in FP64 (its norm gives the stopping test), r32 = (float) r;
+ *   e = 0; inner_cycles V-cycles on A e = r32 entirely in FP32 (the
+ *   stencil_mg_solve cycle with every operation in binary32: FP32 residual
+ *   r = f - (6u - S) * (float)(1/(h*h)), FP32 smoothers, the same transfers
+ *   with float weights); u += (double) e in FP64;
+ * until ||r||/||f|| <= rtol (||r0|| if f = 0) or max_outer iterations.
+ * u (device, FP64) in place; f device or NULL; dims, h, smoother, nu1, nu2,
+ * ncoarse, max_levels as stencil_mg_solve.  *out_rel, *out_iters (host, may
+ * be NULL) get the last relative residual and the outer iterations done.
+ * Returns STENCIL_OK or STENCIL_ERR_NOT_CONVERGED (u holds the last iterate
+ * either way).  Workspace: two FP32 grids of u's size (r32, e), the FP32
+ * coarse levels (about 2/7 of an FP32 grid) and one FP32 residual grid, plus
+ * the FP32 smoothers' own.  Blocking (reads the residual after every outer
+ * iteration).  Same bits as the serial definition. */
+int stencil_solve_mixed_mg(stencil_ctx* ctx, double* u, const double* f, const int64_t dims[3], double h,
+                           int smoother, int nu1, int nu2, int ncoarse, int max_levels, double rtol, int max_outer,
+                           int inner_cycles, double* out_rel, int* out_iters, void* stream);
+
 /* Bound on every device-side wait of the persistent kernels (default 10 s).
  * never_publish >= 0 makes the task at that queue index never publish its
  * completion, so that a test can watch the bound expire and the error come

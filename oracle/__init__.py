@@ -67,9 +67,16 @@ def _lib():
         lib.oracle_mg_restrict_f64.argtypes = [_P, _I64, _I64, _I64, _P]
         lib.oracle_mg_prolong_add_f64.argtypes = [_P, _I64, _I64, _I64, _P]
         lib.oracle_mg_solve_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _I, _I, _I, _I, _I, _D, _I, _P, _P]
+        lib.oracle_residual_f32.argtypes = [_P, _P, _I64, _I64, _I64, _D, _P]
+        lib.oracle_mg_restrict_f32.argtypes = [_P, _I64, _I64, _I64, _P]
+        lib.oracle_mg_prolong_add_f32.argtypes = [_P, _I64, _I64, _I64, _P]
+        lib.oracle_mg_cycles_f32.argtypes = [_P, _P, _I64, _I64, _I64, _D, _I, _I, _I, _I, _I, _I]
+        lib.oracle_solve_mixed_mg.argtypes = [_P, _P, _I64, _I64, _I64, _D, _I, _I, _I, _I, _I, _D, _I, _I, _P, _P]
         for name in ("oracle_jacobi_f64", "oracle_gs_lex_f64", "oracle_gs_rb_f64", "oracle_gs_rb_f32", "oracle_residual_f64",
                      "oracle_jacobi_f32", "oracle_gs_lex_f32", "oracle_solve_mixed", "oracle_solve_f64",
-                     "oracle_mg_restrict_f64", "oracle_mg_prolong_add_f64", "oracle_mg_solve_f64"):
+                     "oracle_mg_restrict_f64", "oracle_mg_prolong_add_f64", "oracle_mg_solve_f64",
+                     "oracle_residual_f32", "oracle_mg_restrict_f32", "oracle_mg_prolong_add_f32", "oracle_mg_cycles_f32",
+                     "oracle_solve_mixed_mg"):
             getattr(lib, name).restype = _I
         _LIB = lib
     return _LIB
@@ -195,15 +202,29 @@ MG_JACOBI = 0  # weighted Jacobi, omega = 6/7 (a = b = 1/7)
 MG_GS = 1      # lexicographic Gauss-Seidel
 
 
+def residual32(u: np.ndarray, f: np.ndarray | None, h: float) -> np.ndarray:
+    """FP32 residual r = f - (6u - sum) * (float)(1/h^2), every operation in binary32 (halo of r zero)."""
+    _check(u, f, np.float32)
+    r = np.zeros_like(u)
+    rc = _lib().oracle_residual_f32(_ptr(u), _ptr(f), *_dims(u), h, _ptr(r))
+    if rc != 0:
+        raise RuntimeError("oracle_residual_f32 rc=%d" % rc)
+    return r
+
+
 def mg_restrict(r: np.ndarray) -> np.ndarray:
     """Full-weighting restriction of the interior of r (odd extents) to the coarse
-    grid of extents (n-1)/2 (zero halo)."""
-    _check(r, None, np.float64)
+    grid of extents (n-1)/2 (zero halo); float64 or float32 by r's dtype."""
     nx, ny, nz = _dims(r)
-    fc = np.zeros(((nz - 1) // 2 + 2, (ny - 1) // 2 + 2, (nx - 1) // 2 + 2))
-    rc = _lib().oracle_mg_restrict_f64(_ptr(r), nx, ny, nz, _ptr(fc))
+    fc = np.zeros(((nz - 1) // 2 + 2, (ny - 1) // 2 + 2, (nx - 1) // 2 + 2), dtype=r.dtype)
+    if r.dtype == np.float32:
+        _check(r, None, np.float32)
+        rc = _lib().oracle_mg_restrict_f32(_ptr(r), nx, ny, nz, _ptr(fc))
+    else:
+        _check(r, None, np.float64)
+        rc = _lib().oracle_mg_restrict_f64(_ptr(r), nx, ny, nz, _ptr(fc))
     if rc != 0:
-        raise RuntimeError("oracle_mg_restrict_f64 rc=%d" % rc)
+        raise RuntimeError("oracle_mg_restrict rc=%d" % rc)
     return fc
 
 
@@ -211,14 +232,16 @@ def mg_prolong_add(u: np.ndarray, e: np.ndarray) -> np.ndarray:
     """u plus the trilinear prolongation of the coarse correction e (zero on the
     coarse boundary); u is not modified."""
     out = np.array(u, copy=True, order="C")
-    _check(out, None, np.float64)
-    _check(e, None, np.float64)
+    dt = np.float32 if out.dtype == np.float32 else np.float64
+    _check(out, None, dt)
+    _check(e, None, dt)
     nx, ny, nz = _dims(out)
     if _dims(e) != ((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2):
         raise ValueError("e must be the coarse grid of u")
-    rc = _lib().oracle_mg_prolong_add_f64(_ptr(out), nx, ny, nz, _ptr(e))
+    fn = _lib().oracle_mg_prolong_add_f32 if dt == np.float32 else _lib().oracle_mg_prolong_add_f64
+    rc = fn(_ptr(out), nx, ny, nz, _ptr(e))
     if rc != 0:
-        raise RuntimeError("oracle_mg_prolong_add_f64 rc=%d" % rc)
+        raise RuntimeError("oracle_mg_prolong_add rc=%d" % rc)
     return out
 
 
@@ -234,3 +257,30 @@ def mg_solve(u: np.ndarray, f: np.ndarray | None, h: float, smoother: int, nu1: 
     if rc not in (0, -5):
         raise RuntimeError("oracle_mg_solve_f64 rc=%d" % rc)
     return out, rel.value, cyc.value, rc == 0
+
+
+def mg_cycles32(u: np.ndarray, f: np.ndarray, h: float, smoother: int, nu1: int, nu2: int, ncoarse: int,
+                max_levels: int, ncycles: int) -> np.ndarray:
+    """Exactly ``ncycles`` FP32 V-cycles on A u = f (float32 arrays); u is not modified."""
+    out = np.array(u, copy=True, order="C")
+    _check(out, f, np.float32)
+    rc = _lib().oracle_mg_cycles_f32(_ptr(out), _ptr(f), *_dims(out), h, smoother, nu1, nu2, ncoarse, max_levels,
+                                     ncycles)
+    if rc != 0:
+        raise RuntimeError("oracle_mg_cycles_f32 rc=%d" % rc)
+    return out
+
+
+def solve_mixed_mg(u: np.ndarray, f: np.ndarray | None, h: float, smoother: int, nu1: int, nu2: int, ncoarse: int,
+                   max_levels: int, rtol: float, max_outer: int, inner_cycles: int):
+    """Defect correction (FP64 residual and update) with ``inner_cycles`` FP32 V-cycles per outer
+    iteration.  Returns (u, rel, outer_iters, converged)."""
+    out = np.array(u, copy=True, order="C")
+    _check(out, f, np.float64)
+    rel = ctypes.c_double(0.0)
+    its = ctypes.c_int(0)
+    rc = _lib().oracle_solve_mixed_mg(_ptr(out), _ptr(f), *_dims(out), h, smoother, nu1, nu2, ncoarse, max_levels,
+                                      rtol, max_outer, inner_cycles, ctypes.addressof(rel), ctypes.addressof(its))
+    if rc not in (0, -5):
+        raise RuntimeError("oracle_solve_mixed_mg rc=%d" % rc)
+    return out, rel.value, its.value, rc == 0

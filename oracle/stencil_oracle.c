@@ -533,3 +533,216 @@ int oracle_mg_solve_f64(double* u, const double* f, int64_t nx, int64_t ny, int6
   if (out_cycles) *out_cycles = it;
   return rel <= rtol ? ORC_OK : ORC_NOT_CONVERGED;
 }
+
+/* ---------------------------------------------------------------------------
+ * Single-precision multigrid and the mixed-precision multigrid solve (not in
+ * the paper; the paper's smoothers inside the multigrid solver that Sec. 1
+ * and Sec. 3 name as their setting, run on binary32 storage inside an FP64
+ * defect correction).
+ *
+ * The FP32 cycle is the FP64 cycle above with every operation in float:
+ *  - residual r = f - (6u - sum) * ih2, ih2 = (float)(1/(h*h)) with 1/(h*h)
+ *    formed in double; 6u is the float product 6.0f*u;
+ *  - smoothers: weighted Jacobi a = b = (float)(1/7), Gauss-Seidel
+ *    b = (float)(1/6), hh = (float)(h*h) (the FP32 sweeps above);
+ *  - restriction and prolongation with the float weights 0.25f, 0.5f in the
+ *    same order as the FP64 transfers.
+ *
+ * Mixed solve (defect correction with an FP32 multigrid inner solver):
+ *   r = f - A u (double); rel = ||r||/||f|| (||r0|| if f == 0)
+ *   while rel > rtol and outer < max_outer:
+ *       r32 = (float) r on the interior; e32 = 0
+ *       inner_cycles FP32 V-cycles on A e = r32 (levels, nu1, nu2, ncoarse
+ *       as the FP64 cycle)
+ *       u += (double) e32 on the interior
+ *       r = f - A u; rel = ...
+ * ------------------------------------------------------------------------- */
+
+/* FP32 residual r = f - (6u - sum) * ih2 on the interior (halo of r untouched). */
+int oracle_residual_f32(const float* u, const float* f, int64_t nx, int64_t ny, int64_t nz, double h, float* r) {
+  orc_grid g;
+  if (!u || !r || orc_grid_make(&g, nx, ny, nz) != ORC_OK || !(h > 0.0)) return ORC_ERR_ARG;
+  const float ih2 = (float)(1.0 / (h * h));
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        size_t c = orc_at(&g, i, j, k);
+        float au = (6.0f * u[c] - orc_sum_s(u, c, g.sx, g.sy)) * ih2;
+        float fv = f ? f[c] : 0.0f;
+        r[c] = fv - au;
+      }
+  return ORC_OK;
+}
+
+/* FP32 full weighting, the same order as oracle_mg_restrict_f64. */
+int oracle_mg_restrict_f32(const float* r, int64_t nx, int64_t ny, int64_t nz, float* fc) {
+  orc_grid gf, gc;
+  if (!r || !fc || orc_grid_make(&gf, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  if (nx % 2 == 0 || ny % 2 == 0 || nz % 2 == 0) return ORC_ERR_ARG;
+  orc_grid_make(&gc, (nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2);
+  for (int64_t K = 0; K < gc.nz; ++K)
+    for (int64_t J = 0; J < gc.ny; ++J)
+      for (int64_t I = 0; I < gc.nx; ++I) {
+        float sy[3];
+        for (int dz = -1; dz <= 1; ++dz) {
+          float sx[3];
+          for (int dy = -1; dy <= 1; ++dy) {
+            size_t c = orc_at(&gf, 2 * I + 1, 2 * J + 1 + dy, 2 * K + 1 + dz);
+            sx[dy + 1] = (0.25f * r[c - 1] + 0.5f * r[c]) + 0.25f * r[c + 1];
+          }
+          sy[dz + 1] = (0.25f * sx[0] + 0.5f * sx[1]) + 0.25f * sx[2];
+        }
+        fc[orc_at(&gc, I, J, K)] = (0.25f * sy[0] + 0.5f * sy[1]) + 0.25f * sy[2];
+      }
+  return ORC_OK;
+}
+
+/* FP32 trilinear prolongation added to u, the same order as the FP64 one. */
+int oracle_mg_prolong_add_f32(float* u, int64_t nx, int64_t ny, int64_t nz, const float* e) {
+  orc_grid gf, gc;
+  if (!u || !e || orc_grid_make(&gf, nx, ny, nz) != ORC_OK) return ORC_ERR_ARG;
+  if (nx % 2 == 0 || ny % 2 == 0 || nz % 2 == 0) return ORC_ERR_ARG;
+  orc_grid_make(&gc, (nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2);
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        const int64_t xa = (i % 2) ? (i - 1) / 2 : i / 2 - 1, xb = (i % 2) ? xa : i / 2;
+        const int64_t ya = (j % 2) ? (j - 1) / 2 : j / 2 - 1, yb = (j % 2) ? ya : j / 2;
+        const int64_t za = (k % 2) ? (k - 1) / 2 : k / 2 - 1, zb = (k % 2) ? za : k / 2;
+        float ey[2];
+        for (int zz = 0; zz < 2; ++zz) {
+          const int64_t Z = zz ? zb : za;
+          float ex[2];
+          for (int yy = 0; yy < 2; ++yy) {
+            const int64_t Y = yy ? yb : ya;
+            const float a = e[orc_at(&gc, xa, Y, Z)];
+            ex[yy] = (i % 2) ? a : (a + e[orc_at(&gc, xb, Y, Z)]) * 0.5f;
+          }
+          ey[zz] = (j % 2) ? ex[0] : (ex[0] + ex[1]) * 0.5f;
+        }
+        const float ez = (k % 2) ? ey[0] : (ey[0] + ey[1]) * 0.5f;
+        const size_t c = orc_at(&gf, i, j, k);
+        u[c] = u[c] + ez;
+      }
+  return ORC_OK;
+}
+
+typedef struct {
+  orc_grid g;
+  double h;
+  float* u;
+  float* f;
+  float* r;
+} orc_level32;
+
+static void orc_mg_smooth32(orc_level32* L, int smoother, int nsweeps) {
+  if (nsweeps <= 0) return;
+  if (smoother == 0)
+    oracle_jacobi_f32(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, (float)(1.0 / 7.0), (float)(1.0 / 7.0), nsweeps);
+  else
+    oracle_gs_lex_f32(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, (float)(1.0 / 6.0), nsweeps);
+}
+
+static void orc_vcycle32(orc_level32* lv, int l, int nlev, int smoother, int nu1, int nu2, int ncoarse) {
+  orc_level32* L = &lv[l];
+  if (l == nlev - 1) {
+    orc_mg_smooth32(L, smoother, ncoarse);
+    return;
+  }
+  orc_level32* C = &lv[l + 1];
+  orc_mg_smooth32(L, smoother, nu1);
+  oracle_residual_f32(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, L->r);
+  oracle_mg_restrict_f32(L->r, L->g.nx, L->g.ny, L->g.nz, C->f);
+  memset(C->u, 0, orc_total(&C->g) * sizeof(float));
+  orc_vcycle32(lv, l + 1, nlev, smoother, nu1, nu2, ncoarse);
+  oracle_mg_prolong_add_f32(L->u, L->g.nx, L->g.ny, L->g.nz, C->u);
+  orc_mg_smooth32(L, smoother, nu2);
+}
+
+/* ncycles FP32 V-cycles on A u = f (u, f float, in place on u); levels as
+ * oracle_mg_solve_f64.  No stopping test: exactly ncycles cycles. */
+int oracle_mg_cycles_f32(float* u, const float* f, int64_t nx, int64_t ny, int64_t nz, double h, int smoother,
+                         int nu1, int nu2, int ncoarse, int max_levels, int ncycles) {
+  orc_grid g0;
+  if (!u || !f || orc_grid_make(&g0, nx, ny, nz) != ORC_OK || !(h > 0.0) || (smoother != 0 && smoother != 1) ||
+      nu1 < 0 || nu2 < 0 || ncoarse < 0 || max_levels < 1 || max_levels > 32 || ncycles < 0)
+    return ORC_ERR_ARG;
+  orc_level32 lv[32];
+  memset(lv, 0, sizeof(lv));
+  int nlev = 1;
+  lv[0].g = g0;
+  lv[0].h = h;
+  lv[0].u = u;
+  lv[0].f = (float*)f;
+  while (nlev < max_levels) {
+    const orc_grid* p = &lv[nlev - 1].g;
+    if (p->nx < 3 || p->ny < 3 || p->nz < 3 || p->nx % 2 == 0 || p->ny % 2 == 0 || p->nz % 2 == 0) break;
+    orc_grid_make(&lv[nlev].g, (p->nx - 1) / 2, (p->ny - 1) / 2, (p->nz - 1) / 2);
+    lv[nlev].h = 2.0 * lv[nlev - 1].h;
+    ++nlev;
+  }
+  int rc = ORC_OK;
+  for (int l = 0; l < nlev; ++l) {
+    const size_t n = orc_total(&lv[l].g);
+    lv[l].r = (float*)calloc(n, sizeof(float));
+    if (l > 0) {
+      lv[l].u = (float*)calloc(n, sizeof(float));
+      lv[l].f = (float*)calloc(n, sizeof(float));
+    }
+    if (!lv[l].r || (l > 0 && (!lv[l].u || !lv[l].f))) rc = ORC_ERR_OOM;
+  }
+  if (rc == ORC_OK)
+    for (int c = 0; c < ncycles; ++c) orc_vcycle32(lv, 0, nlev, smoother, nu1, nu2, ncoarse);
+  for (int l = 0; l < nlev; ++l) {
+    free(lv[l].r);
+    if (l > 0) {
+      free(lv[l].u);
+      free(lv[l].f);
+    }
+  }
+  return rc;
+}
+
+int oracle_solve_mixed_mg(double* u, const double* f, int64_t nx, int64_t ny, int64_t nz, double h, int smoother,
+                          int nu1, int nu2, int ncoarse, int max_levels, double rtol, int max_outer, int inner_cycles,
+                          double* out_rel, int* out_iters) {
+  orc_grid g;
+  if (!u || orc_grid_make(&g, nx, ny, nz) != ORC_OK || !(h > 0.0) || max_outer < 0 || inner_cycles < 0 ||
+      (smoother != 0 && smoother != 1))
+    return ORC_ERR_ARG;
+  size_t n = orc_total(&g);
+  double* r = (double*)calloc(n, sizeof(double));
+  float* r32 = (float*)calloc(n, sizeof(float));
+  float* e32 = (float*)calloc(n, sizeof(float));
+  if (!r || !r32 || !e32) { free(r); free(r32); free(e32); return ORC_ERR_OOM; }
+  double rn = 0.0, fn = 0.0;
+  oracle_residual_f64(u, f, nx, ny, nz, h, r, &rn, &fn);
+  const double denom = fn > 0.0 ? fn : rn;
+  double rel = denom > 0.0 ? rn / denom : 0.0;
+  int it = 0, rc = ORC_OK;
+  while (rel > rtol && it < max_outer) {
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+          size_t c = orc_at(&g, i, j, k);
+          r32[c] = (float)r[c];
+          e32[c] = 0.0f;
+        }
+    rc = oracle_mg_cycles_f32(e32, r32, nx, ny, nz, h, smoother, nu1, nu2, ncoarse, max_levels, inner_cycles);
+    if (rc != ORC_OK) break;
+    for (int64_t k = 0; k < nz; ++k)
+      for (int64_t j = 0; j < ny; ++j)
+        for (int64_t i = 0; i < nx; ++i) {
+          size_t c = orc_at(&g, i, j, k);
+          u[c] = u[c] + (double)e32[c];
+        }
+    ++it;
+    oracle_residual_f64(u, f, nx, ny, nz, h, r, &rn, NULL);
+    rel = denom > 0.0 ? rn / denom : 0.0;
+  }
+  free(r); free(r32); free(e32);
+  if (rc != ORC_OK) return rc;
+  if (out_rel) *out_rel = rel;
+  if (out_iters) *out_iters = it;
+  return rel <= rtol ? ORC_OK : ORC_NOT_CONVERGED;
+}

@@ -113,6 +113,8 @@ _SIGS = {
                                _P]),
     "stencil_mg_solve": (_I, [_P, _P, _P, _I64P, _D, _I, _I, _I, _I, _I, _D, _I, ctypes.POINTER(_D),
                               ctypes.POINTER(_I), _P]),
+    "stencil_solve_mixed_mg": (_I, [_P, _P, _P, _I64P, _D, _I, _I, _I, _I, _I, _D, _I, _I, ctypes.POINTER(_D),
+                                    ctypes.POINTER(_I), _P]),
 }
 
 _LIB = None
@@ -392,6 +394,21 @@ def stencil_mg_solve(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: f
                               int(max_cycles), ctypes.byref(rel), ctypes.byref(cyc), _stream(stream))
     _check(ctx, rc, allow=(STENCIL_ERR_NOT_CONVERGED,))
     return rel.value, cyc.value, rc == STENCIL_OK
+
+
+def stencil_solve_mixed_mg(ctx: Context, u: torch.Tensor, f: torch.Tensor | None, h: float, smoother: int, *,
+                           nu1: int = 2, nu2: int = 2, ncoarse: int = 20, max_levels: int = 32, rtol: float = 1e-10,
+                           max_outer: int = 50, inner_cycles: int = 1, stream=None):
+    """Defect correction with FP32 multigrid V-cycles inside (FP64 residual and update) until the
+    relative residual <= rtol; returns (rel, outer_iters, converged)."""
+    lib = load_library()
+    rel, its = ctypes.c_double(0.0), ctypes.c_int(0)
+    rc = lib.stencil_solve_mixed_mg(ctx.handle, _grid(u, torch.float64), _opt_grid(f, u, torch.float64), _dims(u),
+                                    float(h), int(smoother), int(nu1), int(nu2), int(ncoarse), int(max_levels),
+                                    float(rtol), int(max_outer), int(inner_cycles), ctypes.byref(rel),
+                                    ctypes.byref(its), _stream(stream))
+    _check(ctx, rc, allow=(STENCIL_ERR_NOT_CONVERGED,))
+    return rel.value, its.value, rc == STENCIL_OK
 
 
 # ------------------------------------------------------------------ server --

@@ -38,6 +38,8 @@ enum SlotId {
   SLOT_MG_R,             // multigrid: residual of the level being restricted
   SLOT_JACOBI_SLABS,     // in-place Jacobi: ring of three z-slabs of new values
   SLOT_F_SCALED,         // FP64 sweeps with f: the products hh*f, computed once per call
+  SLOT_MG32_LEVELS,      // mixed multigrid: FP32 correction and right-hand side of every coarse level
+  SLOT_MG32_R,           // mixed multigrid: FP32 residual of the level being restricted
   SLOT_COUNT
 };
 
@@ -108,6 +110,9 @@ int gs_column_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, 
 // pointer of the two sums.
 int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Geom& g, double h,
                     double* r_out, float* r32_out, double** result, cudaStream_t st, bool norm = true);
+// FP32 residual r = f - A u on the interior (every operation in binary32), no norm: the FP32 multigrid levels
+int residual32_launch(stencil_ctx* ctx, const float* u, const float* f, const Geom& g, double h, float* r_out,
+                      cudaStream_t st);
 // copies the two sums of residual_launch to the host (blocking)
 int read_sums(stencil_ctx* ctx, const double* dres, double* sums, cudaStream_t st);
 // u[interior] += (double) e[interior]

@@ -58,6 +58,21 @@ int residual_launch(stencil_ctx* ctx, const double* u, const double* f, const Ge
   return STENCIL_OK;
 }
 
+int residual32_launch(stencil_ctx* ctx, const float* u, const float* f, const Geom& g, double h, float* r_out,
+                      cudaStream_t st) {
+  const dim3 grid = residual_grid(g);
+  if ((int64_t)grid.x * grid.y * grid.z == 0) return STENCIL_OK;
+  const float ih2 = (float)(1.0 / (h * h));
+  if (f)
+    residual_f32_kernel<true><<<grid, dim3(RES_BX, RES_BY), 0, st>>>(u, f, r_out, g, ih2);
+  else
+    residual_f32_kernel<false><<<grid, dim3(RES_BX, RES_BY), 0, st>>>(u, f, r_out, g, ih2);
+  ctx->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "residual_f32_kernel");
+  return STENCIL_OK;
+}
+
 __global__ void correct_kernel(double* __restrict__ u, const float* __restrict__ e, Geom g) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;

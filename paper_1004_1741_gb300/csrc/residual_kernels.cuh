@@ -105,3 +105,32 @@ __global__ void __launch_bounds__(NT) reduce_pairs_kernel(const double* __restri
 }
 
 }  // namespace stn
+
+namespace stn {
+
+// FP32 residual r = f - (6u - S) * ih2 (every operation in binary32, ih2 =
+// (float)(1/(h*h))) on the interior, for the FP32 multigrid levels; no norm.
+template <bool HAS_F>
+__global__ void __launch_bounds__(RES_BX* RES_BY) residual_f32_kernel(const float* __restrict__ u,
+                                                                      const float* __restrict__ f,
+                                                                      float* __restrict__ r_out, Geom g, float ih2) {
+  using Ar = ArithF32;
+  const int x = blockIdx.x * RES_BX + threadIdx.x;
+  const int y = blockIdx.y * RES_BY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int z0 = blockIdx.z * RES_ZCHUNK;
+  const int z1 = min(g.nz, z0 + RES_ZCHUNK);
+  for (int z = z0; z < z1; ++z) {
+    const int64_t c = g.at(x, y, z);
+    float s = Ar::add(u[c - 1], u[c + 1]);
+    s = Ar::add(s, u[c - g.sx]);
+    s = Ar::add(s, u[c + g.sx]);
+    s = Ar::add(s, u[c - g.sy]);
+    s = Ar::add(s, u[c + g.sy]);
+    const float au = __fmul_rn(__fsub_rn(__fmul_rn(6.0f, u[c]), s), ih2);
+    const float fv = HAS_F ? f[c] : 0.0f;
+    r_out[c] = __fsub_rn(fv, au);
+  }
+}
+
+}  // namespace stn

@@ -568,3 +568,197 @@ def test_mg_one_level_is_plain_smoothing():
         np.testing.assert_array_equal(got, oracle.gs_lex(u0, f, h, 5))
         got, _, _, _ = oracle.mg_solve(u0, f, h, oracle.MG_JACOBI, 3, 3, 5, levels, 0.0, 1)
         np.testing.assert_array_equal(got, oracle.jacobi(u0, f, h, 5, a=1.0 / 7.0, b=1.0 / 7.0))
+
+
+# ------------------------------------------------- FP32 sparse forms ----
+def test_gs_red_black_f32_half_sweeps():
+    """FP32 red-black GS against its own definition (each colour a simultaneous update of
+    that colour from the current values, red first), evaluated in float64 from the FP32
+    oracle's own previous colour: every site within a few binary32 roundings.  A colour swap
+    or a wrong neighbour in the FP32 copy moves sites by O(1)."""
+    nx, ny, nz = 6, 5, 4
+    rng = np.random.default_rng(21)
+    u = rng.random((nz + 2, ny + 2, nx + 2)).astype(np.float32)
+    f = rng.standard_normal(u.shape).astype(np.float32)
+    h = 0.2
+    n = F.neighbour_matrix(nx, ny, nz)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    red = ((i + j + k) % 2 == 0).ravel()
+    bnd = F.boundary_sum(u.astype(np.float64))
+    hh = float(np.float32(h * h))
+    x = F.interior(u)
+    out = oracle.gs_rb(u, f, h, 1)
+    assert out.dtype == np.float32
+    for colour in (red, ~red):
+        y = (n @ x + bnd + hh * F.interior(f)) * float(oracle.B32)
+        x = np.where(colour, y, x)
+    scale = np.abs(x).max() + hh * np.abs(f).max()
+    np.testing.assert_allclose(F.interior(out), x, rtol=0, atol=16 * EPS32 * scale)
+    # black only after red: the red half alone differs from the full sweep on black sites
+    y = (n @ F.interior(u) + bnd + hh * F.interior(f)) * float(oracle.B32)
+    assert np.abs(np.where(~red, F.interior(out) - y, 0)).max() > 1e-3
+
+
+@pytest.mark.parametrize("with_f", [False, True])
+def test_jacobi_f32_weighted_sparse_form(with_f):
+    """FP32 weighted Jacobi u' = a u + b (N u + bnd + hh f) with a = b = (float)(1/7): the sparse
+    form in float64 from the same float32 data, within a few binary32 roundings per sweep, and
+    the mode factor a + 6 b mu on a sine mode.  A dropped a*u term, a wrong weight or a wrong
+    neighbour fails by far more."""
+    nx, ny, nz = 7, 6, 5
+    rng = np.random.default_rng(22)
+    u = rng.random((nz + 2, ny + 2, nx + 2)).astype(np.float32)
+    f = rng.standard_normal(u.shape).astype(np.float32) if with_f else None
+    h = 0.125
+    a = b = float(np.float32(1.0 / 7.0))
+    hh = float(np.float32(h * h))
+    n = F.neighbour_matrix(nx, ny, nz)
+    bnd = F.boundary_sum(u.astype(np.float64))
+    x = F.interior(u)
+    for sweeps in range(1, 4):
+        x = a * x + b * (n @ x + bnd + (hh * F.interior(f) if with_f else 0.0))
+        out = oracle.jacobi(u, f, h, sweeps, a=a, b=b)
+        assert out.dtype == np.float32
+        scale = np.abs(x).max() + (hh * np.abs(f).max() if with_f else 0.0)
+        np.testing.assert_allclose(F.interior(out), x, rtol=0, atol=8 * sweeps * EPS32 * scale)
+    phi = F.sine_mode(nx, ny, nz, 2, 1, 3).astype(np.float32)
+    mu = F.jacobi_factor(nx, ny, nz, 2, 1, 3)
+    out = oracle.jacobi(phi, None, 1.0, 2, a=a, b=b)
+    np.testing.assert_allclose(out.astype(np.float64), (a + 6 * b * mu) ** 2 * phi.astype(np.float64), rtol=0,
+                               atol=32 * EPS32)
+
+
+# -------------------------------------------- FP32 and mixed multigrid ----
+def test_residual_f32_eigenrelation_and_sparse_form():
+    """FP32 residual: r = f - lambda phi for a sine mode, and the sparse form (6u - N u - bnd)/h^2
+    on random data, both within binary32 rounding of the FP32 operations; a harmonic polynomial
+    with small integer values (exact in float32) has r exactly 0 with f = 0."""
+    nx, ny, nz = 8, 6, 7
+    h = 1.0 / 9
+    phi = F.sine_mode(nx, ny, nz, 2, 3, 1)
+    lam = F.eigenvalue(nx, ny, nz, 2, 3, 1, h)
+    f = np.random.default_rng(2).standard_normal(phi.shape)
+    r = oracle.residual32(phi.astype(np.float32), f.astype(np.float32), h)
+    assert r.dtype == np.float32
+    ref = F.interior(f.astype(np.float32)) - lam * F.interior(phi.astype(np.float32))
+    np.testing.assert_allclose(F.interior(r), ref, rtol=0, atol=64 * EPS32 * (lam + np.abs(f).max()))
+    assert r[0].max() == 0 and r[-1].max() == 0
+    rng = np.random.default_rng(23)
+    u = rng.random((nz + 2, ny + 2, nx + 2)).astype(np.float32)
+    r = oracle.residual32(u, None, 0.15)
+    au = (6.0 * F.interior(u) - F.neighbour_matrix(nx, ny, nz) @ F.interior(u) - F.boundary_sum(u.astype(np.float64)))
+    au = au * float(np.float32(1.0 / (0.15 * 0.15)))
+    np.testing.assert_allclose(F.interior(r), -au, rtol=0, atol=64 * EPS32 * np.abs(au).max() + 1e-30)
+    for name, field in F.harmonic_fields(nx, ny, nz).items():
+        if name in ("x+2y-3z", "x2-y2", "xy+yz+zx"):
+            r = oracle.residual32(field.astype(np.float32), None, 0.5)
+            assert not np.any(r), name
+
+
+@pytest.mark.parametrize("dims", [(7, 5, 9), (11, 3, 7)])
+def test_mg_f32_transfers_are_exact_on_linear_functions(dims):
+    """FP32 full weighting and trilinear prolongation: a linear function with dyadic values (exact
+    in float32, as every intermediate 1/4 and 1/2 multiple is) is reproduced exactly, the 27
+    restriction weights are the products of (1/4, 1/2, 1/4), and a coarse spike prolongs to the
+    product of hats -- the FP64 transfers' pins, now on the binary32 copies."""
+    nx, ny, nz = dims
+    for fn in (lambda i, j, k: 0 * i + 3.0, lambda i, j, k: i + 2.0 * j - 3.0 * k + 0.5):
+        r = _fill_interior(_padded(nx, ny, nz), fn).astype(np.float32)
+        fc = oracle.mg_restrict(r)
+        assert fc.dtype == np.float32
+        want = _fill_interior(_padded((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2),
+                              lambda I, J, K: fn(2 * I + 1, 2 * J + 1, 2 * K + 1))
+        np.testing.assert_array_equal(fc, want.astype(np.float32))
+    w1 = lambda d: np.where(d == 0, 0.5, np.where(np.abs(d) == 1, 0.25, 0.0))
+    I, J, K = 1, min(1, (ny - 1) // 2 - 1), 1
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                fi, fj, fk = 2 * I + 1 + dx, 2 * J + 1 + dy, 2 * K + 1 + dz
+                r = _padded(nx, ny, nz).astype(np.float32)
+                r[fk + 1, fj + 1, fi + 1] = 1.0
+                want = _fill_interior(_padded((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2),
+                                      lambda Ic, Jc, Kc: w1(fi - (2 * Ic + 1)) * w1(fj - (2 * Jc + 1)) *
+                                      w1(fk - (2 * Kc + 1)))
+                np.testing.assert_array_equal(oracle.mg_restrict(r), want.astype(np.float32))
+    g = lambda i, j, k: 0.5 * i - 2.0 * j + 3.0 * k + 1.25
+    e = _fill_interior(_padded((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2),
+                       lambda I, J, K: g(2 * I + 1, 2 * J + 1, 2 * K + 1)).astype(np.float32)
+    u = oracle.mg_prolong_add(_padded(nx, ny, nz).astype(np.float32), e)
+    assert u.dtype == np.float32
+    want = _fill_interior(_padded(nx, ny, nz), g)
+    np.testing.assert_array_equal(u[2:-2, 2:-2, 2:-2], want[2:-2, 2:-2, 2:-2].astype(np.float32))
+    e = _padded((nx - 1) // 2, (ny - 1) // 2, (nz - 1) // 2).astype(np.float32)
+    e[1, 1, 2] = 1.0  # coarse (I, J, K) = (1, 0, 0)
+    u = oracle.mg_prolong_add(_padded(nx, ny, nz).astype(np.float32), e)
+    hat = lambda x, c: np.maximum(0.0, 1.0 - np.abs(x - c) / 2.0)
+    want = _fill_interior(_padded(nx, ny, nz), lambda i, j, k: hat(i, 3) * hat(j, 1) * hat(k, 1))
+    np.testing.assert_array_equal(u, want.astype(np.float32))
+
+
+@pytest.mark.parametrize("smoother,bound", [(oracle.MG_GS, 0.2), (oracle.MG_JACOBI, 0.32)])
+def test_mg_f32_vcycle_reduces_the_error_by_a_fixed_factor(smoother, bound):
+    """The FP32 V(2,2) cycle on the zero-data Laplace problem shrinks a random error by the
+    textbook grid-independent factor while the error is far above the binary32 floor."""
+    rng = np.random.default_rng(8)
+    for n in (15, 31):
+        u = _padded(n, n, n).astype(np.float32)
+        u[1:-1, 1:-1, 1:-1] = rng.random((n, n, n))
+        f = np.zeros_like(u)
+        prev = np.abs(u).max()
+        for _ in range(4):
+            u = oracle.mg_cycles32(u, f, 1.0 / (n + 1), smoother, 2, 2, 10, 8, 1)
+            cur = float(np.abs(u).max())
+            assert cur <= bound * prev
+            prev = cur
+
+
+def test_mg_f32_one_level_is_plain_fp32_smoothing():
+    rng = np.random.default_rng(4)
+    for dims, levels in (((7, 5, 9), 1), ((8, 7, 7), 6)):
+        nx, ny, nz = dims
+        u0 = rng.random((nz + 2, ny + 2, nx + 2)).astype(np.float32)
+        f = _padded(nx, ny, nz).astype(np.float32)
+        f[1:-1, 1:-1, 1:-1] = rng.standard_normal((nz, ny, nx))
+        h = 0.1
+        got = oracle.mg_cycles32(u0, f, h, oracle.MG_GS, 3, 3, 5, levels, 1)
+        np.testing.assert_array_equal(got, oracle.gs_lex(u0, f, h, 5))
+        got = oracle.mg_cycles32(u0, f, h, oracle.MG_JACOBI, 3, 3, 5, levels, 1)
+        np.testing.assert_array_equal(got, oracle.jacobi(u0, f, h, 5, a=float(np.float32(1 / 7)),
+                                                         b=float(np.float32(1 / 7))))
+
+
+@pytest.mark.parametrize("smoother", [oracle.MG_GS, oracle.MG_JACOBI])
+def test_solve_mixed_mg_reaches_closed_form(smoother):
+    """Defect correction with FP32 V-cycles inside: the FP64 residual reaches 1e-11 and u the
+    closed-form discrete solution u* = sum a phi / lambda, in about as many outer iterations as
+    the FP64 multigrid needs cycles; FP32 cycles alone (one outer iteration, many cycles) stall
+    near the binary32 floor, so the FP64 correction is what reaches FP64 accuracy."""
+    n = 31
+    h, f, ustar = _sine_rhs(n, [(1, 1, 1), (2, 1, 3), (5, 7, 2)], [1.0, -0.7, 0.4])
+    u, rel, outer, ok = oracle.solve_mixed_mg(np.zeros_like(f), f, h, smoother, 2, 2, 20, 8, 1e-11, 40, 1)
+    assert ok and rel <= 1e-11
+    assert np.abs(u - ustar).max() <= 1e-9 * np.abs(ustar).max()
+    _, _, cycles, _ = oracle.mg_solve(np.zeros_like(f), f, h, smoother, 2, 2, 20, 8, 1e-11, 40)
+    assert outer <= cycles + 3, (outer, cycles)
+    _, rel1, _, ok1 = oracle.solve_mixed_mg(np.zeros_like(f), f, h, smoother, 2, 2, 20, 8, 1e-11, 1, 30)
+    assert not ok1 and rel1 > 1e-9
+
+
+def test_solve_mixed_mg_one_outer_step_is_its_definition():
+    """One outer iteration equals the steps written out with the pinned pieces: r from the FP64
+    residual, rounded to float32, FP32 cycles from zero, u + (double) e."""
+    n = 15
+    rng = np.random.default_rng(5)
+    u0 = _padded(n, n, n)
+    u0[1:-1, 1:-1, 1:-1] = rng.random((n, n, n))
+    f = _padded(n, n, n)
+    f[1:-1, 1:-1, 1:-1] = rng.standard_normal((n, n, n))
+    h = 1.0 / (n + 1)
+    got, _, its, _ = oracle.solve_mixed_mg(u0, f, h, oracle.MG_GS, 2, 2, 10, 8, 0.0, 1, 2)
+    assert its == 1
+    r, _, _ = oracle.residual(u0, f, h)
+    e = oracle.mg_cycles32(np.zeros(u0.shape, np.float32), r.astype(np.float32), h, oracle.MG_GS, 2, 2, 10, 8, 2)
+    want = u0.copy()
+    want[1:-1, 1:-1, 1:-1] += e[1:-1, 1:-1, 1:-1].astype(np.float64)
+    np.testing.assert_array_equal(got, want)
