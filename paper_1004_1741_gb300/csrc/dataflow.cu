@@ -199,7 +199,7 @@ static int plan_build(stencil_ctx* ctx, DFPlan* pl, int kind, int n, const Geom*
 }
 
 template <typename T>
-static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, int D, const SiteTable& tb,
+static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, int D, int nt, const SiteTable& tb,
                         int int_adds, bool any_f, bool pre_f) {
   cudaStream_t gs = ctx->gstream;
   cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
@@ -207,7 +207,7 @@ static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, in
   int rc = STENCIL_OK;
   e = cudaMemsetAsync(pl->dev + pl->b_desc + pl->b_task, 0, pl->b_flag + 256, gs);
   if (e == cudaSuccess && kind == DF_KIND_GS_COLUMN) {
-    rc = df_column_launch<T>(ctx, pl->run, W, H, int_adds, any_f, pre_f, gs);
+    rc = df_column_launch<T>(ctx, pl->run, W, H, nt, int_adds, any_f, pre_f, gs);
   } else if (e == cudaSuccess) {
     rc = STENCIL_UNSUPPORTED_TILE;
 #define DF_TILE(WW, HH, DD)                                                                          \
@@ -305,7 +305,7 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
   if (!pl->exec || pl->exec_timeout != timeout_ns || pl->exec_poison != poison || pl->exec_tb != tb.coords) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     pl->exec = nullptr;
-    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, tb, int_adds, any_f, pre_f);
+    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, nt, tb, int_adds, any_f, pre_f);
     if (rc) return rc;
     pl->exec_timeout = timeout_ns;
     pl->exec_poison = poison;

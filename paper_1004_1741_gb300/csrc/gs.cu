@@ -329,19 +329,42 @@ template <typename T, class Ar>
 static int gs_tiles(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz, int nt,
                     int nsweeps, bool direct, cudaStream_t st);
 
-// Column march (gs_column.cu) with the integer-pipe share of the additions.
+// Column march (gs_column.cu; nt 2..4: gs_column_ns.cuh) with the integer-pipe share of the additions.
+template <typename T, class Ar>
+static int gs_column_go(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int nt, int tx, int ty, int tz,
+                        int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st, bool pre_f = false) {
+  if (nt == 1) return gs_column_run<T, Ar>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
+  if (nt == 2) return gs_column_ns_run<T, Ar, 2>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
+  if (nt == 3) return gs_column_ns_run<T, Ar, 3>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
+  return gs_column_ns_run<T, Ar, 4>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
+}
+
 template <typename T>
-static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
+static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps, int nt,
                               const stencil_params* p, cudaStream_t st) {
   Coef<T> c;
   c.a = T(0);
   c.b = (T)((p && p->b != 0.0) ? p->b : 1.0 / 6.0);
   c.hh = (T)(h * h);
-  const int tx = p ? p->tile_x : 0, ty = p ? p->tile_y : 0, tz = p ? p->tile_z : 0;
+  int tx = p ? p->tile_x : 0, ty = p ? p->tile_y : 0, tz = p ? p->tile_z : 0;
   const bool persistent = p && p->variant == 5;
   const int int_adds = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsColumn;
   if (int_adds < 0 || int_adds > kIntAddsAdaptive)
     return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..6)", int_adds);
+  if (nt > 1) {
+    // several sweeps per task: tiles 8x8 (FP64) / 16x8 (FP32), chunks as the one-sweep march (at least nt planes)
+    if (tx == 0) tx = sizeof(T) == 8 ? 8 : 16;
+    if (ty == 0) ty = 8;
+    if (tz <= 0) {
+      const int cap = nsweeps < 8 ? 16 : 100;
+      const int chunks = (g.nz + cap - 1) / cap;
+      tz = (g.nz + chunks - 1) / chunks;
+    }
+    if (tz < nt) tz = nt;
+    if (sizeof(T) == 8 && int_adds != 0 && int_adds != 2 && int_adds != kIntAddsAdaptive)
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column march with %d sweeps per task: int_adds = %d (0, 2 or 6)",
+                     nt, int_adds);
+  }
   if constexpr (sizeof(T) == 8) {
     // f over several sweeps: hh*f once into workspace, the sweeps add it as it is (one FP64 multiplication
     // per site fewer; at int_adds 0, 2 and 6, and only when the workspace budget has room for it)
@@ -353,24 +376,28 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
         ctx->launches++;
         if (e != cudaSuccess) return cuda_err(ctx, e, "prescale_f launch");
         if (int_adds == kIntAddsAdaptive)
-          return gs_column_run<T, AdaptColumnPre>(ctx, u, w, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st,
-                                                  true);
+          return gs_column_go<T, AdaptColumnPre>(ctx, u, w, g, c, nt, tx, ty, tz, nsweeps, persistent, int_adds, h,
+                                                 st, true);
         if (int_adds == 2)
-          return gs_column_run<T, ArithPreF<ArithF64Mix<0x15u>>>(ctx, u, w, g, c, tx, ty, tz, nsweeps, persistent,
-                                                                 int_adds, h, st, true);
-        return gs_column_run<T, ArithPreF<ArithF64Fma>>(ctx, u, w, g, c, tx, ty, tz, nsweeps, persistent, int_adds,
-                                                        h, st, true);
+          return gs_column_go<T, ArithPreF<ArithF64Mix<0x15u>>>(ctx, u, w, g, c, nt, tx, ty, tz, nsweeps, persistent,
+                                                                int_adds, h, st, true);
+        return gs_column_go<T, ArithPreF<ArithF64Fma>>(ctx, u, w, g, c, nt, tx, ty, tz, nsweeps, persistent,
+                                                       int_adds, h, st, true);
       }
     }
-    if (int_adds == 1) return gs_column_run<T, ArithF64Mix<0x1Du>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
-    if (int_adds == 2) return gs_column_run<T, ArithF64Mix<0x15u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
-    if (int_adds == 3) return gs_column_run<T, ArithF64Mix<0x12u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
-    if (int_adds == 4) return gs_column_run<T, ArithF64Mix<0x10u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
-    if (int_adds == 5) return gs_column_run<T, ArithF64Mix<0x00u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+    if (nt == 1) {
+      if (int_adds == 1) return gs_column_run<T, ArithF64Mix<0x1Du>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+      if (int_adds == 3) return gs_column_run<T, ArithF64Mix<0x12u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+      if (int_adds == 4) return gs_column_run<T, ArithF64Mix<0x10u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+      if (int_adds == 5) return gs_column_run<T, ArithF64Mix<0x00u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+    }
+    if (int_adds == 2)
+      return gs_column_go<T, ArithF64Mix<0x15u>>(ctx, u, f, g, c, nt, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
     if (int_adds == kIntAddsAdaptive)
-      return gs_column_run<T, AdaptColumn>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+      return gs_column_go<T, AdaptColumn>(ctx, u, f, g, c, nt, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
   }
-  return gs_column_run<T, typename DefaultArith<T>::type>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
+  return gs_column_go<T, typename DefaultArith<T>::type>(ctx, u, f, g, c, nt, tx, ty, tz, nsweeps, persistent,
+                                                         int_adds, h, st);
 }
 
 template <typename T>
@@ -385,8 +412,8 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
   // one sweep per pass without an explicit tile: the column march is the default
   const bool tiled = p && (p->tile_x || p->tile_y || p->tile_z);
   if (variant == 4 || variant == 5 || (variant == 0 && nt == 1 && !tiled)) {
-    if (nt != 1) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column-march Gauss-Seidel runs nt = 1 only");
-    return gs_column_dispatch<T>(ctx, u, f, g, h, nsweeps, p, st);
+    if (nt > 4) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column-march Gauss-Seidel runs nt = 1..4");
+    return gs_column_dispatch<T>(ctx, u, f, g, h, nsweeps, nt, p, st);
   }
   const int tx = (p && p->tile_x) ? p->tile_x : 16;
   const int ty = (p && p->tile_y) ? p->tile_y : 16;

@@ -246,8 +246,12 @@ static int df_column_tile(stencil_ctx* ctx, const DFRun& run, int tx, int ty, bo
 }
 
 template <typename T>
-int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, bool pre_f,
+int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int nt, int int_adds, bool any_f, bool pre_f,
                      cudaStream_t st) {
+  if (nt == 2) return df_column_ns_launch<T, 2>(ctx, run, tx, ty, int_adds, any_f, pre_f, st);
+  if (nt == 3) return df_column_ns_launch<T, 3>(ctx, run, tx, ty, int_adds, any_f, pre_f, st);
+  if (nt == 4) return df_column_ns_launch<T, 4>(ctx, run, tx, ty, int_adds, any_f, pre_f, st);
+  if (nt != 1) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column march with %d sweeps per task (1..4)", nt);
   if constexpr (sizeof(T) == 8) {
     if (pre_f) {  // f holds hh*f
       if (int_adds == kIntAddsAdaptive) return df_column_tile<T, AdaptColumnPre>(ctx, run, tx, ty, any_f, st);
@@ -264,8 +268,8 @@ int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int
   }
   return df_column_tile<T, typename DefaultArith<T>::type>(ctx, run, tx, ty, any_f, st);
 }
-template int df_column_launch<double>(stencil_ctx*, const DFRun&, int, int, int, bool, bool, cudaStream_t);
-template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, bool, bool, cudaStream_t);
+template int df_column_launch<double>(stencil_ctx*, const DFRun&, int, int, int, int, bool, bool, cudaStream_t);
+template int df_column_launch<float>(stencil_ctx*, const DFRun&, int, int, int, int, bool, bool, cudaStream_t);
 
 // Column-march Gauss-Seidel: tiles tx x ty columns (8x8, 8x16, 16x8; default 8x8 for FP64, whose FP64
 // pipe favours the short ramp of narrow tiles, 16x8 for FP32) x tz planes (default: equal chunks of at

@@ -147,10 +147,19 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
 // Gauss-Seidel task (gs_column.cu; nt = 1, tile W x H columns x D planes)
 constexpr int DF_KIND_GS_COLUMN = 16;
 struct DFRun;
-// launch of the persistent column-march kernel for one dataflow run (gs_column.cu)
+// launch of the persistent column-march kernel for one dataflow run (gs_column.cu); pre_f: the grids' f
+// arrays hold hh*f (offered at int_adds 0, 2 and 6); nt > 1: tasks of nt sweeps each (gs_column_ns.cuh)
 template <typename T>
-// (pre_f: the grids' f arrays hold hh*f; offered at int_adds 0 and 2)
-int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, bool pre_f,
+int df_column_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int nt, int int_adds, bool any_f, bool pre_f,
                      cudaStream_t st);
+
+// Column march with NS = 2..4 sweeps per task (gs_column_ns.cuh; instantiated per NS in gs_column_ns<NS>.cu):
+// level launches or one persistent dataflow launch; tiles 8x8 and 16x8
+template <typename T, class Ar, int NS>
+int gs_column_ns_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int tx, int ty, int tz,
+                     int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st, bool pre_f);
+template <typename T, int NS>
+int df_column_ns_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int int_adds, bool any_f, bool pre_f,
+                        cudaStream_t st);
 
 }  // namespace stn

@@ -189,16 +189,54 @@ def test_gs_column_int_adds(ctx, int_adds, variant):
                   oracle.gs_lex(u1, f1, 0.2, 5), "gs column random int_adds=%d" % int_adds)
 
 
+@pytest.mark.parametrize("dims", RAGGED + [(45, 38, 29), (70, 9, 33), (20, 20, 2), (17, 18, 3), (2, 2, 2)])
+@pytest.mark.parametrize("tile", [(0, 0, 0), (8, 8, 7), (16, 8, 0), (8, 8, 1), (16, 8, 2), (8, 8, 1000)])
+@pytest.mark.parametrize("nt", [2, 3, 4])
+@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_gs_column_march_several_sweeps_per_task(ctx, dims, tile, nt, variant, dtype):
+    """The column march with nt sweeps per task (sweep s on the tile shifted by -s, two steps behind
+    sweep s - 1, one shared-memory ring): level launches and the persistent launch, ragged tiles,
+    chunks shorter than nt (raised to nt), sweep counts below, at and above multiples of nt, with and
+    without f."""
+    u0, f0 = W.random_grid(*dims, seed=13, dtype=dtype, with_f=True)
+    for ns, ff in ((1, f0), (nt, None), (2 * nt + 1, f0), (5, None)):
+        _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, ff, 0.04, ns, nt=nt, tile=tile, variant=variant),
+                      oracle.gs_lex(u0, ff, 0.04, ns),
+                      "gs column nt=%d v%d %s %s ns=%d" % (nt, variant, dims, tile, ns))
+
+
+@pytest.mark.parametrize("int_adds", [0, 2, 6])
+@pytest.mark.parametrize("nt", [2, 4])
+@pytest.mark.parametrize("variant", [4, 5])
+def test_gs_column_several_sweeps_int_adds(ctx, int_adds, nt, variant):
+    """Every integer-pipe form the multi-sweep march offers (0, 2, adaptive) gives the oracle's bits:
+    the positive Laplace field, a random field with f (h^2 f once per call), Poisson data of both
+    signs from u = 0."""
+    u0 = W.laplace_cube(70, 1, 2)
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, None, 1.0, 9, nt=nt, variant=variant, int_adds=int_adds),
+                  oracle.gs_lex(u0, None, 1.0, 9), "gs column nt=%d laplace int_adds=%d" % (nt, int_adds))
+    u1, f1 = W.random_grid(41, 35, 30, seed=int_adds, with_f=True)
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u1, f1, 0.2, 5, nt=nt, variant=variant, int_adds=int_adds,
+                       tile=(16, 8, 9)),
+                  oracle.gs_lex(u1, f1, 0.2, 5), "gs column nt=%d random int_adds=%d" % (nt, int_adds))
+    u2 = np.zeros_like(u1)
+    _assert_exact(_run(ctx, capi.stencil_gs_lex, u2, f1, 0.2, 6, nt=nt, variant=variant, int_adds=int_adds),
+                  oracle.gs_lex(u2, f1, 0.2, 6), "gs column nt=%d both signs int_adds=%d" % (nt, int_adds))
+
+
 def test_gs_column_rejects_nt(ctx):
     u = _dev(W.random_grid(9, 9, 9, seed=1)[0])
     with pytest.raises(capi.StencilError):
-        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, nt=2, variant=4)
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, nt=5, variant=4)
     with pytest.raises(capi.StencilError):
         capi.stencil_gs_lex(ctx, u, None, 1.0, 4, tile=(32, 16, 0), variant=4)
     with pytest.raises(capi.StencilError):
         capi.stencil_gs_lex(ctx, u, None, 1.0, 4, tile=(32, 16, 0), variant=5)
     with pytest.raises(capi.StencilError):
-        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, nt=2, variant=5)
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, nt=2, variant=5, tile=(8, 16, 0))
+    with pytest.raises(capi.StencilError):
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 4, nt=2, variant=4, int_adds=3)
     with pytest.raises(capi.StencilError):
         capi.stencil_gs_lex(ctx, u, None, 1.0, 4, variant=6)
 
@@ -406,21 +444,21 @@ def test_batched_prescaled_f(ctx):
             _assert_exact(us[i].cpu().numpy(), ofn(u0, f0, h, ns), "batched %d grid %d" % (sm, i))
 
 
-@pytest.mark.parametrize("variant", [3, 5])
-def test_dataflow_wait_bound_reports_timeout(variant):
+@pytest.mark.parametrize("variant,nt", [(3, 1), (5, 1), (5, 2)])
+def test_dataflow_wait_bound_reports_timeout(variant, nt):
     """A task whose completion is never published: the bounded waits expire, the
-    call returns STENCIL_ERR_TIMEOUT, and the context keeps working (tile tasks
-    and column-march tasks)."""
+    call returns STENCIL_ERR_TIMEOUT, and the context keeps working (tile tasks,
+    column-march tasks of one and of two sweeps)."""
     c = capi.Context(0)
     u0, _ = W.random_grid(40, 40, 40, seed=1)
     u = _dev(u0)
     capi.stencil_set_wait_limit(c, 50_000_000, never_publish=3)
     with pytest.raises(capi.StencilError) as e:
-        capi.stencil_gs_lex(c, u, None, 1.0, 4, variant=variant)
+        capi.stencil_gs_lex(c, u, None, 1.0, 4, nt=nt, variant=variant)
     assert e.value.code == capi.STENCIL_ERR_TIMEOUT
     capi.stencil_set_wait_limit(c, 10_000_000_000, never_publish=-1)
-    _assert_exact(_run(c, capi.stencil_gs_lex, u0, None, 1.0, 4, variant=variant), oracle.gs_lex(u0, None, 1.0, 4),
-                  "after")
+    _assert_exact(_run(c, capi.stencil_gs_lex, u0, None, 1.0, 4, nt=nt, variant=variant),
+                  oracle.gs_lex(u0, None, 1.0, 4), "after")
     c.close()
 
 
