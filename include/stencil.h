@@ -359,8 +359,7 @@ void stencil_server_destroy(stencil_server* srv);
 /* Self-check of the integer-arithmetic binary64 addition and multiplication:
  * n pairs drawn from a counter-based generator seeded by `seed` (random
  * magnitudes, ties, carries, zeros, signs), each summed on the integer pipes
- * (the symmetric form, the ordered form in both argument orders, and the
- * branch-free forms of both, which must accept the same pairs) and
+ * (the symmetric form, and the ordered form in both argument orders) and
  * multiplied in integer arithmetic (both orders, random signs), against the
  * FP64 pipe.  *out_mismatch (host) receives the number of results whose bits
  * differ (must be 0), *out_fast the number of pairs the symmetric addition

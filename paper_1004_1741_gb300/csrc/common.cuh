@@ -120,56 +120,6 @@ __device__ __forceinline__ bool int_add_f64_ge(double a, double b, double* out) 
   return true;
 }
 
-// Branch-free forms of the two additions: the integer sequence always runs
-// (shift distances kept in range when the operands fall outside the fast
-// path), *ok is cleared when it does not give the IEEE sum, and the caller
-// discards the result then.  Several independent updates can so be issued as
-// one straight-line sequence and repaired afterwards on the rare failure.
-__device__ __forceinline__ double int_add_f64_nb(double a, double b, bool* ok) {
-  const unsigned ahi = (unsigned)__double2hiint(a), alo = (unsigned)__double2loint(a);
-  const unsigned bhi = (unsigned)__double2hiint(b), blo = (unsigned)__double2loint(b);
-  const bool sw = (bhi >> 20) > (ahi >> 20);
-  const unsigned hhi = sw ? bhi : ahi, hlo = sw ? blo : alo;
-  const unsigned lhi = sw ? ahi : bhi, llo = sw ? alo : blo;
-  const unsigned eh = hhi >> 20;
-  const unsigned d = eh - (lhi >> 20);
-  const bool good = (eh - 11u) < 2035u && d <= 10u;
-  *ok = *ok && good;
-  const unsigned mh = (hhi & 0xFFFFFu) | 0x100000u, ml = (lhi & 0xFFFFFu) | 0x100000u;
-  const unsigned sh = 10u - (good ? d : 0u);
-  const unsigned long long MH = ((unsigned long long)__funnelshift_l(hlo, mh, 10) << 32) | (hlo << 10);
-  const unsigned long long ML = ((unsigned long long)__funnelshift_l(llo, ml, sh) << 32) | (llo << sh);
-  const unsigned long long S = MH + ML;
-  const unsigned shi = (unsigned)(S >> 32), slo = (unsigned)S;
-  const unsigned c = shi >> 31;
-  const unsigned s2lo = __funnelshift_r(slo, shi, c) | (slo & c), s2hi = shi >> c;
-  const unsigned long long R = (((unsigned long long)s2hi << 32) | s2lo) + (0x1FFu + ((s2lo >> 10) & 1u));
-  const unsigned rlo = (unsigned)R, rhi = (unsigned)(R >> 32);
-  const unsigned mlo = __funnelshift_r(rlo, rhi, 10), mhi = (rhi >> 10) + ((eh + c - 1u) << 20);
-  return __hiloint2double((int)mhi, (int)mlo);
-}
-
-__device__ __forceinline__ double int_add_f64_ge_nb(double a, double b, bool* ok) {
-  const unsigned hhi = (unsigned)__double2hiint(a), hlo = (unsigned)__double2loint(a);
-  const unsigned lhi = (unsigned)__double2hiint(b), llo = (unsigned)__double2loint(b);
-  const unsigned eh = hhi >> 20;
-  const unsigned d = eh - (lhi >> 20);
-  const bool good = (eh - 11u) < 2035u && d <= 10u;
-  *ok = *ok && good;
-  const unsigned mh = (hhi & 0xFFFFFu) | 0x100000u, ml = (lhi & 0xFFFFFu) | 0x100000u;
-  const unsigned sh = 10u - (good ? d : 0u);
-  const unsigned long long MH = ((unsigned long long)__funnelshift_l(hlo, mh, 10) << 32) | (hlo << 10);
-  const unsigned long long ML = ((unsigned long long)__funnelshift_l(llo, ml, sh) << 32) | (llo << sh);
-  const unsigned long long S = MH + ML;
-  const unsigned shi = (unsigned)(S >> 32), slo = (unsigned)S;
-  const unsigned c = shi >> 31;
-  const unsigned s2lo = __funnelshift_r(slo, shi, c) | (slo & c), s2hi = shi >> c;
-  const unsigned long long R = (((unsigned long long)s2hi << 32) | s2lo) + (0x1FFu + ((s2lo >> 10) & 1u));
-  const unsigned rlo = (unsigned)R, rhi = (unsigned)(R >> 32);
-  const unsigned mlo = __funnelshift_r(rlo, rhi, 10), mhi = (rhi >> 10) + ((eh + c - 1u) << 20);
-  return __hiloint2double((int)mhi, (int)mlo);
-}
-
 // Binary64 multiplication carried out in integer arithmetic (the 64-bit
 // products on the integer multiply-add path, the rest on the ALU pipe): the
 // IEEE round-to-nearest-even product when both operands are normal and the
@@ -304,40 +254,6 @@ __device__ __forceinline__ T site_update_warp(bool active, T w, T e, T s, T n, T
     return active ? site_update<T, Ar, HAS_F, WEIGHTED>(w, e, s, n, bo, t, fv, uc, c) : T(0);
   }
 }
-
-// FP64 arithmetic in two phases for kernels that issue several independent
-// updates per step: fast() takes the additions whose bit is clear in
-// NATIVE_MASK on the integer pipes without any branch and reports whether all
-// of them were exact; the caller recomputes the updates that were not with
-// SLOW (same bits either way: every path gives the IEEE result).  PRE_F: f
-// holds hh*f (the site update adds it as it is).
-template <unsigned NATIVE_MASK, class SLOW, bool PRE_F = false>
-struct ArithDeferred : SLOW {
-  using Slow = SLOW;
-  static __device__ __forceinline__ double f_term(double hh, double fv) {
-    return PRE_F ? fv : ArithF64Fma::mul(hh, fv);
-  }
-  template <bool HAS_F>
-  static __device__ __forceinline__ double fast(double w, double e, double s, double n, double bo, double t,
-                                                double fv, const Coef<double>& c, bool* ok) {
-    double acc = (NATIVE_MASK & 1u) ? ArithF64Fma::add(w, e) : int_add_f64_nb(w, e, ok);
-    acc = (NATIVE_MASK & 2u) ? ArithF64Fma::add(acc, s) : int_add_f64_ge_nb(acc, s, ok);
-    acc = (NATIVE_MASK & 4u) ? ArithF64Fma::add(acc, n) : int_add_f64_ge_nb(acc, n, ok);
-    acc = (NATIVE_MASK & 8u) ? ArithF64Fma::add(acc, bo) : int_add_f64_ge_nb(acc, bo, ok);
-    acc = (NATIVE_MASK & 16u) ? ArithF64Fma::add(acc, t) : int_add_f64_ge_nb(acc, t, ok);
-    if (HAS_F) acc = ArithF64Fma::add(acc, f_term(c.hh, fv));
-    return ArithF64Fma::mul(c.b, acc);
-  }
-};
-
-template <class Ar>
-struct DeferOf {
-  static constexpr bool on = false;
-};
-template <unsigned M, class S, bool P>
-struct DeferOf<ArithDeferred<M, S, P>> {
-  static constexpr bool on = true;
-};
 
 // Asynchronous element copy global -> shared (cp.async, through L1) and its
 // group bookkeeping: wait until at most N of this thread's groups are pending.

@@ -24,8 +24,6 @@
 #include <algorithm>
 #include <vector>
 
-#include <type_traits>
-
 #include "internal.h"
 #include "tiles.h"
 #include "task_bodies.cuh"
@@ -335,20 +333,10 @@ static int gs_tiles(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c
 template <typename T, class Ar>
 static int gs_column_go(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> c, int nt, int tx, int ty, int tz,
                         int nsweeps, bool persistent, int int_adds, double h, cudaStream_t st, bool pre_f = false) {
-  // the one-sweep march takes every form but the two-phase ones; the multi-sweep march the two-phase forms
-  // (int_adds 2, 3), the adaptive form, all-FP64 and FP32
-  constexpr bool one = !DeferOf<Ar>::on;
-  constexpr bool multi = !std::is_same<Ar, ArithF64Mix<0x15u>>::value &&
-                         !std::is_same<Ar, ArithPreF<ArithF64Mix<0x15u>>>::value;
-  if constexpr (one) {
-    if (nt == 1) return gs_column_run<T, Ar>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
-  }
-  if constexpr (multi) {
-    if (nt == 2) return gs_column_ns_run<T, Ar, 2>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
-    if (nt == 3) return gs_column_ns_run<T, Ar, 3>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
-    if (nt == 4) return gs_column_ns_run<T, Ar, 4>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
-  }
-  return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column march: int_adds = %d with nt = %d", int_adds, nt);
+  if (nt == 1) return gs_column_run<T, Ar>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
+  if (nt == 2) return gs_column_ns_run<T, Ar, 2>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
+  if (nt == 3) return gs_column_ns_run<T, Ar, 3>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
+  return gs_column_ns_run<T, Ar, 4>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st, pre_f);
 }
 
 template <typename T>
@@ -368,17 +356,14 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
     if (tx == 0) tx = sizeof(T) == 8 ? 8 : 16;
     if (ty == 0) ty = 8;
     if (tz <= 0) {
-      // the shifted boxes span nz + nt - 1 planes: equal chunks of at most cap + nt - 1 of them, so that no
-      // chunk holds only the last sweeps' shifted planes
-      const int cap = (nsweeps < 8 ? 16 : 100) + nt - 1;
-      const int span = g.nz + nt - 1;
-      const int chunks = (span + cap - 1) / cap;
-      tz = (span + chunks - 1) / chunks;
+      const int cap = nsweeps < 8 ? 16 : 100;
+      const int chunks = (g.nz + cap - 1) / cap;
+      tz = (g.nz + chunks - 1) / chunks;
     }
     if (tz < nt) tz = nt;
-    if (sizeof(T) == 8 && int_adds != 0 && int_adds != 2 && int_adds != 3 && int_adds != kIntAddsAdaptive)
-      return set_err(ctx, STENCIL_ERR_UNSUPPORTED,
-                     "column march with %d sweeps per task: int_adds = %d (0, 2, 3 or 6)", nt, int_adds);
+    if (sizeof(T) == 8 && int_adds != 0 && int_adds != 2 && int_adds != kIntAddsAdaptive)
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column march with %d sweeps per task: int_adds = %d (0, 2 or 6)",
+                     nt, int_adds);
   }
   if constexpr (sizeof(T) == 8) {
     // f over several sweeps: hh*f once into workspace, the sweeps add it as it is (one FP64 multiplication
@@ -393,9 +378,6 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
         if (int_adds == kIntAddsAdaptive)
           return gs_column_go<T, AdaptColumnPre>(ctx, u, w, g, c, nt, tx, ty, tz, nsweeps, persistent, int_adds, h,
                                                  st, true);
-        if (int_adds == 2 && nt > 1)
-          return gs_column_go<T, DeferColumnPre>(ctx, u, w, g, c, nt, tx, ty, tz, nsweeps, persistent, int_adds, h,
-                                                 st, true);
         if (int_adds == 2)
           return gs_column_go<T, ArithPreF<ArithF64Mix<0x15u>>>(ctx, u, w, g, c, nt, tx, ty, tz, nsweeps, persistent,
                                                                 int_adds, h, st, true);
@@ -409,10 +391,6 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
       if (int_adds == 4) return gs_column_run<T, ArithF64Mix<0x10u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
       if (int_adds == 5) return gs_column_run<T, ArithF64Mix<0x00u>>(ctx, u, f, g, c, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
     }
-    if (int_adds == 2 && nt > 1)
-      return gs_column_go<T, DeferColumn2>(ctx, u, f, g, c, nt, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
-    if (int_adds == 3 && nt > 1)
-      return gs_column_go<T, DeferColumn3>(ctx, u, f, g, c, nt, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
     if (int_adds == 2)
       return gs_column_go<T, ArithF64Mix<0x15u>>(ctx, u, f, g, c, nt, tx, ty, tz, nsweeps, persistent, int_adds, h, st);
     if (int_adds == kIntAddsAdaptive)

@@ -174,59 +174,24 @@ __device__ __forceinline__ void gs_column_ns_body(T* u, const T* __restrict__ f,
       }
     }
     cp_async_commit();
-    if constexpr (DeferOf<Ar>::on) {
-      // all NS updates as one straight-line sequence (integer-pipe additions without branches), then
-      // the rare repair on the fallback arithmetic and the stores
-      T v[NS];
-      bool ok[NS];
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        int q = st - 2 * s;
-        if (q < 0) q += R;
-        const int qm = q == 0 ? R - 1 : q - 1, qp = wrap(q);
-        const int pos = up_pos[s];
-        const T* pm = ring + qm * PL + pos;
-        const T* pp = ring + qp * PL + pos;
+    for (int s = 0; s < NS; ++s) {
+      const bool act = up_win[s].in(t);
+      int q = st - 2 * s;
+      if (q < 0) q += R;
+      const int qm = q == 0 ? R - 1 : q - 1, qp = wrap(q);
+      const int pos = up_pos[s];
+      const T* pm = ring + qm * PL + pos;
+      const T* pp = ring + qp * PL + pos;
+      if constexpr (AdaptOf<Ar>::on) {  // the warp votes; every lane reads inside the ring
         const T fv = HAS_F ? fring[q * FPL + up_fpos[s]] : T(0);
-        ok[s] = true;
-        v[s] = Ar::template fast<HAS_F>(pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv, c, &ok[s]);
-      }
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        if (!up_win[s].in(t)) continue;
-        int q = st - 2 * s;
-        if (q < 0) q += R;
-        const int pos = up_pos[s];
-        if (!ok[s]) {
-          const int qm = q == 0 ? R - 1 : q - 1, qp = wrap(q);
-          const T* pm = ring + qm * PL + pos;
-          const T* pp = ring + qp * PL + pos;
-          const T fv = HAS_F ? fring[q * FPL + up_fpos[s]] : T(0);
-          v[s] = site_update<T, typename Ar::Slow, HAS_F, false>(pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv,
-                                                                T(0), c);
-        }
-        ring[q * PL + pos] = v[s];
-      }
-    } else {
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        const bool act = up_win[s].in(t);
-        int q = st - 2 * s;
-        if (q < 0) q += R;
-        const int qm = q == 0 ? R - 1 : q - 1, qp = wrap(q);
-        const int pos = up_pos[s];
-        const T* pm = ring + qm * PL + pos;
-        const T* pp = ring + qp * PL + pos;
-        if constexpr (AdaptOf<Ar>::on) {  // the warp votes; every lane reads inside the ring
-          const T fv = HAS_F ? fring[q * FPL + up_fpos[s]] : T(0);
-          const T vv = site_update_warp<T, Ar, HAS_F, false>(act, pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv,
-                                                             T(0), c);
-          if (act) ring[q * PL + pos] = vv;
-        } else if (act) {
-          const T fv = HAS_F ? fring[q * FPL + up_fpos[s]] : T(0);
-          ring[q * PL + pos] =
-              site_update<T, Ar, HAS_F, false>(pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv, T(0), c);
-        }
+        const T v = site_update_warp<T, Ar, HAS_F, false>(act, pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv,
+                                                          T(0), c);
+        if (act) ring[q * PL + pos] = v;
+      } else if (act) {
+        const T fv = HAS_F ? fring[q * FPL + up_fpos[s]] : T(0);
+        ring[q * PL + pos] =
+            site_update<T, Ar, HAS_F, false>(pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv, T(0), c);
       }
     }
 #pragma unroll
@@ -364,16 +329,15 @@ int df_column_ns_launch(stencil_ctx* ctx, const DFRun& run, int tx, int ty, int 
   if constexpr (sizeof(T) == 8) {
     if (pre_f) {
       if (int_adds == kIntAddsAdaptive) return df_column_ns_tile<T, AdaptColumnPre, NS>(ctx, run, tx, ty, any_f, st);
-      if (int_adds == 2) return df_column_ns_tile<T, DeferColumnPre, NS>(ctx, run, tx, ty, any_f, st);
+      if (int_adds == 2) return df_column_ns_tile<T, ArithPreF<ArithF64Mix<0x15u>>, NS>(ctx, run, tx, ty, any_f, st);
       if (int_adds == 0) return df_column_ns_tile<T, ArithPreF<ArithF64Fma>, NS>(ctx, run, tx, ty, any_f, st);
       return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "prescaled f with int_adds = %d (0, 2 or 6)", int_adds);
     }
     if (int_adds == kIntAddsAdaptive) return df_column_ns_tile<T, AdaptColumn, NS>(ctx, run, tx, ty, any_f, st);
-    if (int_adds == 2) return df_column_ns_tile<T, DeferColumn2, NS>(ctx, run, tx, ty, any_f, st);
-    if (int_adds == 3) return df_column_ns_tile<T, DeferColumn3, NS>(ctx, run, tx, ty, any_f, st);
+    if (int_adds == 2) return df_column_ns_tile<T, ArithF64Mix<0x15u>, NS>(ctx, run, tx, ty, any_f, st);
     if (int_adds != 0)
-      return set_err(ctx, STENCIL_ERR_UNSUPPORTED,
-                     "column march with %d sweeps per task: int_adds = %d (0, 2, 3 or 6)", NS, int_adds);
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column march with %d sweeps per task: int_adds = %d (0, 2 or 6)",
+                     NS, int_adds);
   }
   return df_column_ns_tile<T, typename DefaultArith<T>::type, NS>(ctx, run, tx, ty, any_f, st);
 }
@@ -411,12 +375,9 @@ int gs_column_ns_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> 
   template int gs_column_ns_run<double, ArithF64Fma, NS>(stencil_ctx*, double*, const double*, const Geom&,          \
                                                          Coef<double>, int, int, int, int, bool, int, double,        \
                                                          cudaStream_t, bool);                                        \
-  template int gs_column_ns_run<double, DeferColumn2, NS>(stencil_ctx*, double*, const double*, const Geom&,         \
-                                                          Coef<double>, int, int, int, int, bool, int, double,       \
-                                                          cudaStream_t, bool);                                       \
-  template int gs_column_ns_run<double, DeferColumn3, NS>(stencil_ctx*, double*, const double*, const Geom&,         \
-                                                          Coef<double>, int, int, int, int, bool, int, double,       \
-                                                          cudaStream_t, bool);                                       \
+  template int gs_column_ns_run<double, ArithF64Mix<0x15u>, NS>(stencil_ctx*, double*, const double*, const Geom&,   \
+                                                                Coef<double>, int, int, int, int, bool, int, double, \
+                                                                cudaStream_t, bool);                                 \
   template int gs_column_ns_run<double, AdaptColumn, NS>(stencil_ctx*, double*, const double*, const Geom&,          \
                                                          Coef<double>, int, int, int, int, bool, int, double,        \
                                                          cudaStream_t, bool);                                        \
@@ -426,9 +387,10 @@ int gs_column_ns_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, Coef<T> 
   template int gs_column_ns_run<double, ArithPreF<ArithF64Fma>, NS>(stencil_ctx*, double*, const double*,            \
                                                                     const Geom&, Coef<double>, int, int, int, int,   \
                                                                     bool, int, double, cudaStream_t, bool);          \
-  template int gs_column_ns_run<double, DeferColumnPre, NS>(stencil_ctx*, double*, const double*, const Geom&,       \
-                                                            Coef<double>, int, int, int, int, bool, int, double,     \
-                                                            cudaStream_t, bool);                                     \
+  template int gs_column_ns_run<double, ArithPreF<ArithF64Mix<0x15u>>, NS>(stencil_ctx*, double*, const double*,     \
+                                                                           const Geom&, Coef<double>, int, int, int, \
+                                                                           int, bool, int, double, cudaStream_t,     \
+                                                                           bool);                                    \
   template int gs_column_ns_run<float, ArithF32, NS>(stencil_ctx*, float*, const float*, const Geom&, Coef<float>,   \
                                                      int, int, int, int, bool, int, double, cudaStream_t, bool);     \
   }

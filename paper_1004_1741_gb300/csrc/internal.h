@@ -135,11 +135,6 @@ using AdaptJacobi = ArithAdaptive<ArithF64Mix<0x12u>, ArithF64Mix<0x1Fu, true>>;
 using AdaptJacobiPre = ArithAdaptive<ArithPreF<ArithF64Mix<0x12u>>, ArithPreF<ArithF64Mix<0x1Fu, true>>>;
 using AdaptColumn = ArithAdaptive<ArithF64Mix<0x15u>, ArithF64Mix<0x1Fu, true>>;
 using AdaptColumnPre = ArithAdaptive<ArithPreF<ArithF64Mix<0x15u>>, ArithPreF<ArithF64Mix<0x1Fu, true>>>;
-// the multi-sweep column march's fixed integer-pipe forms (gs_column_ns.cuh): the NS updates of a step as
-// one branch-free sequence, repaired on the FP64 pipe where an integer-pipe addition does not apply
-using DeferColumn2 = ArithDeferred<0x15u, ArithF64Fma>;
-using DeferColumn3 = ArithDeferred<0x12u, ArithF64Fma>;
-using DeferColumnPre = ArithDeferred<0x15u, ArithPreF<ArithF64Fma>, true>;
 void dataflow_release(stencil_ctx* ctx);  // internal: no kernel instantiated for a tile shape
 
 // Persistent dataflow run of the skewed-tile schedule over n grids (dataflow.cu).

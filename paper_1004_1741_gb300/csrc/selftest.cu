@@ -1,6 +1,5 @@
 // Self-check of the integer-pipe binary64 additions (common.cuh int_add_f64 and
-// its ordered form int_add_f64_ge, and their branch-free forms int_add_f64_nb,
-// int_add_f64_ge_nb) and of the integer-arithmetic multiplication
+// its ordered form int_add_f64_ge) and of the integer-arithmetic multiplication
 // (int_mul_f64) against the FP64 pipe on generated operand pairs.
 #include "internal.h"
 
@@ -55,21 +54,6 @@ __global__ void selftest_int_add_kernel(unsigned long long n, unsigned long long
     // the ordered form, in both argument orders
     if (int_add_f64_ge(a, b, &em) && __double_as_longlong(em) != __double_as_longlong(ref)) ++mism;
     if (int_add_f64_ge(b, a, &em) && __double_as_longlong(em) != __double_as_longlong(__dadd_rn(b, a))) ++mism;
-    // the branch-free forms: the same pairs qualify, and those give the same bits
-    {
-      double e2;
-      bool ok = true;
-      const double nb = int_add_f64_nb(a, b, &ok);
-      if (ok != int_add_f64(a, b, &e2) || (ok && __double_as_longlong(nb) != __double_as_longlong(ref))) ++mism;
-      ok = true;
-      const double nbg = int_add_f64_ge_nb(a, b, &ok);
-      if (ok != int_add_f64_ge(a, b, &e2) || (ok && __double_as_longlong(nbg) != __double_as_longlong(ref))) ++mism;
-      ok = true;
-      const double nbr = int_add_f64_ge_nb(b, a, &ok);
-      if (ok != int_add_f64_ge(b, a, &e2) ||
-          (ok && __double_as_longlong(nbr) != __double_as_longlong(__dadd_rn(b, a))))
-        ++mism;
-    }
     // the integer-path multiplication, on the same pair with independent random signs
     const double sa = ((r3 >> 17) & 1ull) ? -a : a, sb = ((r3 >> 18) & 1ull) ? -b : b;
     if (int_mul_f64(sa, sb, &em) && __double_as_longlong(em) != __double_as_longlong(__dmul_rn(sa, sb))) ++mism;
