@@ -371,27 +371,39 @@ def launch_counts(ctx, smoother, cfg):
     return n
 
 
+def _nt_cfg(name, nt):
+    """Launch parameters of one point of the temporal-depth sweep: the headline configuration at nt = 1;
+    Gauss-Seidel at nt = 2..4 as the persistent column march with nt sweeps per task (8x8 columns FP64 with
+    the headline's integer-pipe form, 16x8 FP32); deeper blocking and Jacobi at nt > 1 the library defaults."""
+    base = HEADLINE["gs" if name.startswith("gs") else "jacobi"]
+    f32 = name.endswith("f32")
+    if name.startswith("gs") and nt <= 4:
+        if nt == 1 and not f32:
+            return dict(tile=base["tile"], variant=base["variant"], int_adds=base["int_adds"])
+        return dict(tile=(16, 8, 0) if f32 else (8, 8, 0), variant=5, int_adds=-1 if f32 else base["int_adds"])
+    if nt == 1:
+        return dict(tile=base["tile"], variant=base["variant"], int_adds=base["int_adds"])
+    return dict(tile=(0, 0, 0), variant=0, int_adds=-1)
+
+
 def nt_sweep(ctx, capi, torch, uj, ug, stream):
     out = {}
-    for name, fn, u, cfg in (("jacobi", capi.stencil_jacobi, uj, HEADLINE["jacobi"]),
-                             ("gs", capi.stencil_gs_lex, ug, HEADLINE["gs"]),
-                             ("jacobi_f32", capi.stencil_jacobi, uj.float(), HEADLINE["jacobi"]),
-                             ("gs_f32", capi.stencil_gs_lex, ug.float(), HEADLINE["gs"])):
+    for name, fn, u in (("jacobi", capi.stencil_jacobi, uj), ("gs", capi.stencil_gs_lex, ug),
+                        ("jacobi_f32", capi.stencil_jacobi, uj.float()), ("gs_f32", capi.stencil_gs_lex, ug.float())):
         res = {}
         for nt in NT_SWEEP:
+            cfg = _nt_cfg(name, nt)
             try:
-                tile = cfg["tile"] if nt == cfg["nt"] else (0, 0, 0)
-                variant = cfg["variant"] if nt == cfg["nt"] else 0
-                ia = cfg["int_adds"] if nt == cfg["nt"] else -1
-                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, variant=variant, int_adds=ia, stream=stream)  # warm
+                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, stream=stream, **cfg)  # warm
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, tile=tile, variant=variant, int_adds=ia, stream=stream)
+                fn(ctx, u, None, 1.0, SWEEPS, nt=nt, stream=stream, **cfg)
                 b.record(stream)
                 torch.cuda.synchronize()
                 t = a.elapsed_time(b) / 1e3
                 res[str(nt)] = {"glups": SWEEPS * N ** 3 / t / 1e9, "ms": t * 1e3,
-                                "alg_bytes_per_lup": (8.0 if u.dtype == torch.float32 else 16.0) / nt}
+                                "alg_bytes_per_lup": (8.0 if u.dtype == torch.float32 else 16.0) / nt,
+                                "variant": cfg["variant"], "tile": list(cfg["tile"])}
             except capi.StencilError as e:
                 res[str(nt)] = {"unsupported": str(e)}
         out[name] = res
@@ -400,8 +412,9 @@ def nt_sweep(ctx, capi, torch, uj, ug, stream):
 
 def batched_compare(ctx, capi, torch, dev, stream, count=256):
     """256 uneven Poisson grids (extents multiples of 16 in [32,192], seed 3): the
-    plain per-grid loop of single-grid calls vs one batched persistent launch,
-    50 Jacobi and 20 Gauss-Seidel sweeps, FP64."""
+    plain per-grid loop of single-grid calls vs one batched persistent launch with the
+    library defaults and with the parameters the autotuner picks on the median grid,
+    50 Jacobi and 20 Gauss-Seidel sweeps, FP64; speedup = plain / the faster batched."""
     from paper_1004_1741_gb300 import workloads
 
     cases = workloads.batched_poisson(count)
@@ -426,13 +439,27 @@ def batched_compare(ctx, capi, torch, dev, stream, count=256):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1e3
 
+    # the autotuner runs on the batch's median grid (by sites) with the batch's sweep count
+    order = sorted(range(count), key=lambda i: cases[i].nx * cases[i].ny * cases[i].nz)
+    mid = order[count // 2]
     for name, sm, sweeps, single in (("jacobi", capi.STENCIL_JACOBI, 50, capi.stencil_jacobi),
                                      ("gs", capi.STENCIL_GS, 20, capi.stencil_gs_lex)):
         t_plain = timed(lambda: [single(ctx, u, f, h, sweeps, stream=stream) for u, f, h in zip(us, fs, hs)])
         t_batch = timed(lambda: capi.stencil_batched(ctx, us, fs, hs, [sweeps] * count, sm, stream=stream))
+        params, tune_glups = capi.stencil_autotune(ctx, sm, us[mid], fs[mid], hs[mid], sweeps, stream=stream)
+        try:
+            t_tuned = timed(lambda: capi.stencil_batched(ctx, us, fs, hs, [sweeps] * count, sm, stream=stream,
+                                                         **params))
+        except capi.StencilError as e:  # a single-grid choice the batched call does not offer
+            t_tuned, params = None, {**params, "batched": str(e)}
         lup = sites * sweeps
+        best = min(t_batch, t_tuned) if t_tuned else t_batch
         out[name] = {"sweeps": sweeps, "plain_glups": lup / t_plain / 1e9, "batched_glups": lup / t_batch / 1e9,
-                     "speedup": t_plain / t_batch}
+                     "autotuned": {"params": {k: (list(v) if isinstance(v, tuple) else v) for k, v in params.items()},
+                                   "median_grid": [cases[mid].nx, cases[mid].ny, cases[mid].nz],
+                                   "single_grid_glups": tune_glups,
+                                   "batched_glups": lup / t_tuned / 1e9 if t_tuned else None},
+                     "speedup": t_plain / best}
     del us, fs, saved
     torch.cuda.empty_cache()
     return out

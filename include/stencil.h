@@ -110,15 +110,19 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          accepted by Jacobi (weighted Jacobi, a = 1 - omega, b = omega/6).
  *  variant kernel variant: 0 = default; Gauss-Seidel 1 = tile staged in
  *          shared memory, 2 = tile updated in place through the L1 cache
- *          (one launch per tile level), 4 = column march: nt = 1 tasks of
- *          tile_x x tile_y columns (8x8, 8x16, 16x8) x tile_z planes, one
- *          thread per column marching up the tile-local wavefront through a
- *          shared-memory ring (one launch per task level);
+ *          (one launch per tile level), 4 = column march: tasks of
+ *          tile_x x tile_y columns x tile_z planes, one thread per column
+ *          marching up the tile-local wavefront through a shared-memory ring
+ *          (one launch per task level); nt = 1: tiles 8x8, 8x16, 16x8;
+ *          nt = 2..4: tiles 8x8, 16x8, every task applying its nt sweeps in
+ *          one march (sweep s on the tile shifted by -s, two steps behind
+ *          sweep s-1; FP64 int_adds 0, 2 or 6);
  *          5 = the column march as one persistent dataflow launch over the
  *          tasks (blocking, like 3; no launch boundary between levels);
- *          Gauss-Seidel default: variant 4 at nt = 1 without a tile (8x8
+ *          Gauss-Seidel default: variant 4 at nt = 1..4 without a tile (8x8
  *          for FP64, 16x8 for FP32, chunks of at most 100 planes, 16 for
- *          calls of fewer than 8 sweeps), variant 2 otherwise;
+ *          calls of fewer than 8 sweeps), variant 2 otherwise (up to
+ *          nt = 16; variant 1 takes FP64 up to nt = 8);
  *          3 (both smoothers) = one persistent
  *          dataflow launch over a dependency-ordered task queue (blocking);
  *          Jacobi 1 = z-march, 2 = z-march with asynchronous plane copies,
@@ -218,9 +222,9 @@ int residual_norm(stencil_ctx* ctx, const double* u, const double* f, const int6
  * STENCIL_F32 (u and f are double* or float* accordingly).  Every grid ends
  * exactly as after stencil_jacobi / stencil_gs_lex with the same arguments.
  * params (may be NULL): nt, tile, b and int_adds shared by all grids
- * (defaults nt = 1; Gauss-Seidel at nt = 1: column-march tasks of 8x8
- * columns (16x8 for FP32) x 100 planes unless variant is 1..3, else 16^3
- * tile tasks; Jacobi 32x4 (FP64) or 32x8 (FP32) z-march columns at nt = 1,
+ * (defaults nt = 1; Gauss-Seidel at nt = 1..4: column-march tasks of 8x8
+ * columns (16x8 for FP32) x 100 + nt - 1 planes, each task applying its nt
+ * sweeps, unless variant is 1..3, else 16^3 tile tasks; Jacobi 32x4 (FP64) or 32x8 (FP32) z-march columns at nt = 1,
  * else 32x8x8 tile tasks; FP64 int_adds: the adaptive form); a must be 0.
  * Jacobi takes a workspace of the total size of the batch, FP64 with f a
  * further one for h^2 f when the budget has room.  Blocking: returns when the

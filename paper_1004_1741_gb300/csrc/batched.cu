@@ -22,15 +22,20 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
     total += (size_t)geoms[(size_t)i].sy * (size_t)(geoms[(size_t)i].nz + 2);
   }
   const int nt = (p && p->nt > 0) ? p->nt : 1;
-  // Gauss-Seidel with one sweep per pass runs the column-march tasks unless a tile-task variant is asked for
-  const bool column = smoother == STENCIL_GS && nt == 1 && (!p || p->variant == 0 || p->variant >= 4);
+  // Gauss-Seidel with one to four sweeps per pass runs the column-march tasks unless a tile-task variant is
+  // asked for (nt > 1: tasks of nt sweeps, gs_column_ns.cuh)
+  const bool column = smoother == STENCIL_GS && nt <= 4 && (!p || p->variant == 0 || p->variant >= 4);
   if (column) {
     if (p && p->a != 0.0) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "weighted sweeps are not batched");
     const int cx = (p && p->tile_x) ? p->tile_x : (sizeof(T) == 8 ? 8 : 16);
     const int cy = (p && p->tile_y) ? p->tile_y : 8;
-    const int cz = (p && p->tile_z) ? p->tile_z : 100;
+    int cz = (p && p->tile_z) ? p->tile_z : 100 + nt - 1;
+    if (cz < nt) cz = nt;
     const int ia = (p && p->int_adds >= 0) ? p->int_adds : kDefaultIntAddsColumn;
     if (ia > kIntAddsAdaptive) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "int_adds = %d (supported 0..6)", ia);
+    if (nt > 1 && sizeof(T) == 8 && ia != 0 && ia != 2 && ia != kIntAddsAdaptive)
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column march with %d sweeps per task: int_adds = %d (0, 2 or 6)",
+                     nt, ia);
     std::vector<T*> a((size_t)n);
     std::vector<const T*> fs((size_t)n);
     for (int i = 0; i < n; ++i) {
@@ -62,7 +67,7 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
       }
     }
     return dataflow_run<T>(ctx, DF_KIND_GS_COLUMN, n, a.data(), nullptr, fs.data(), geoms.data(), nsweeps, h, cx, cy,
-                           cz, 1, ctx->df_timeout_ns, ctx->df_poison, st, (double)(T)bco, ia, pre);
+                           cz, nt, ctx->df_timeout_ns, ctx->df_poison, st, (double)(T)bco, ia, pre);
   }
   // Jacobi with one sweep per pass: one z-march launch per sweep over all grids unless a task variant is asked for
   if (smoother == STENCIL_JACOBI && nt == 1 && (!p || p->variant == 0)) {
@@ -175,6 +180,11 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
       for (int ty : {8, 16}) cands.push_back({4, 1, 8, ty, 0, ia});
       cands.push_back({4, 1, 16, 8, 0, ia});
       cands.push_back({5, 1, 0, 0, 0, ia});  // the same as one persistent launch
+      for (int nt : {2, 3, 4})                // tasks of nt sweeps in one march
+        for (int tx : {8, 16}) {
+          cands.push_back({4, nt, tx, 8, 0, ia});
+          cands.push_back({5, nt, tx, 8, 0, ia});
+        }
     }
     const int nts[] = {1, 2, 4, 8};
     const int tiles[][3] = {{16, 16, 16}, {32, 8, 8}, {32, 16, 16}};

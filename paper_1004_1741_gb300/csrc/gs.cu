@@ -356,9 +356,12 @@ static int gs_column_dispatch(stencil_ctx* ctx, T* u, const T* f, const Geom& g,
     if (tx == 0) tx = sizeof(T) == 8 ? 8 : 16;
     if (ty == 0) ty = 8;
     if (tz <= 0) {
-      const int cap = nsweeps < 8 ? 16 : 100;
-      const int chunks = (g.nz + cap - 1) / cap;
-      tz = (g.nz + chunks - 1) / chunks;
+      // the shifted boxes span nz + nt - 1 planes: equal chunks of at most cap + nt - 1 of them, so that no
+      // chunk holds only the last sweeps' shifted planes
+      const int cap = (nsweeps < 8 ? 16 : 100) + nt - 1;
+      const int span = g.nz + nt - 1;
+      const int chunks = (span + cap - 1) / cap;
+      tz = (span + chunks - 1) / chunks;
     }
     if (tz < nt) tz = nt;
     if (sizeof(T) == 8 && int_adds != 0 && int_adds != 2 && int_adds != kIntAddsAdaptive)
@@ -411,14 +414,16 @@ int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nswe
   if (variant < 0 || variant > 5) return set_err(ctx, STENCIL_ERR_ARG, "variant = %d", variant);
   // one sweep per pass without an explicit tile: the column march is the default
   const bool tiled = p && (p->tile_x || p->tile_y || p->tile_z);
-  if (variant == 4 || variant == 5 || (variant == 0 && nt == 1 && !tiled)) {
+  if (variant == 4 || variant == 5 || (variant == 0 && nt <= 4 && !tiled)) {
     if (nt > 4) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "column-march Gauss-Seidel runs nt = 1..4");
     return gs_column_dispatch<T>(ctx, u, f, g, h, nsweeps, nt, p, st);
   }
   const int tx = (p && p->tile_x) ? p->tile_x : 16;
   const int ty = (p && p->tile_y) ? p->tile_y : 16;
   const int tz = (p && p->tile_z) ? p->tile_z : 16;
-  const int maxnt = sizeof(T) == 8 ? 8 : 16;
+  // the staged box of variant 1 holds (W+nt+1)(H+nt+1)(D+nt+1) values in shared memory: FP64 stops at nt = 8;
+  // the tasks updated through L1 (variants 2, 3) take nt up to 16 with either dtype
+  const int maxnt = (sizeof(T) == 8 && variant == 1) ? 8 : 16;
   const bool direct = variant != 1;
   if (variant == 3) {
     T* const a[1] = {u};

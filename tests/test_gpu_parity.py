@@ -250,6 +250,35 @@ def test_gs_f32_temporal(ctx, nt, variant):
                   oracle.gs_lex(u0, f0, 0.03, ns), "gs f32")
 
 
+@pytest.mark.parametrize("nt", [8, 16])
+def test_gs_f64_deep_temporal_blocking(ctx, nt):
+    """FP64 Gauss-Seidel with 8 and 16 sweeps per pass on 16^3 skewed tiles through L1 (variant 2, the
+    default at nt > 4) and as one persistent launch (variant 3)."""
+    u0, f0 = W.random_grid(45, 38, 40, seed=nt, with_f=True)
+    ns = nt + 3
+    ref = oracle.gs_lex(u0, f0, 0.05, ns)
+    for variant in (0, 3):
+        _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, f0, 0.05, ns, nt=nt, tile=(16, 16, 16), variant=variant), ref,
+                      "gs f64 nt=%d variant %d" % (nt, variant))
+
+
+@pytest.mark.parametrize("nt", [2, 4])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_batched_gs_several_sweeps_per_task(ctx, nt, dtype):
+    """Batched Gauss-Seidel with nt sweeps per column-march task: uneven grids (some with f, some not,
+    sweep counts below and above nt, an empty grid) each equal to the oracle."""
+    dims = [(33, 20, 17), (8, 8, 8), (50, 9, 31), (1, 1, 1), (17, 40, 5)]
+    sweeps = [nt + 1, 1, 2 * nt, 0, 3]
+    grids = [W.random_grid(*d, seed=i, dtype=dtype, with_f=(i % 2 == 0)) for i, d in enumerate(dims)]
+    us = [_dev(u) for u, _ in grids]
+    fs = [_dev(f) for _, f in grids]
+    hs = [W.grid_h(*d) for d in dims]
+    capi.stencil_batched(ctx, us, fs, hs, sweeps, capi.STENCIL_GS, nt=nt)
+    torch.cuda.synchronize()
+    for i, (u0, f0) in enumerate(grids):
+        _assert_exact(us[i].cpu().numpy(), oracle.gs_lex(u0, f0, hs[i], sweeps[i]), "batched gs nt=%d grid %d" % (nt, i))
+
+
 def test_gs_laplace_config1(ctx):
     u0 = W.laplace_64()
     _assert_exact(_run(ctx, capi.stencil_gs_lex, u0, None, 1.0, 10), oracle.gs_lex(u0, None, 1.0, 10), "gs config1")
@@ -544,6 +573,9 @@ def test_argument_errors(ctx):
     assert e.value.code == capi.STENCIL_ERR_ARG
     with pytest.raises(capi.StencilError) as e:
         capi.stencil_gs_lex(ctx, u, None, 1.0, 1, nt=9, tile=(8, 8, 8))
+    assert e.value.code == capi.STENCIL_ERR_UNSUPPORTED
+    with pytest.raises(capi.StencilError) as e:
+        capi.stencil_gs_lex(ctx, u, None, 1.0, 1, nt=16, tile=(16, 16, 16), variant=1)
     assert e.value.code == capi.STENCIL_ERR_UNSUPPORTED
 
 
