@@ -49,9 +49,11 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 pipe peak derived from the unit counts and clock: 152 SMs x 2 FP64 lanes per
-# clock x 2070 MHz = 629.3 G FP64 operations/s (the 1.25 TFLOP/s datasheet figure
-# counts an FMA as two).  Each add or multiply of the site update is one operation.
+# The roofline the bench reports divides by rates measured in the same run
+# (measured_peaks: the library's throughput probes).  For context it also gives the
+# figure derived from unit counts and clocks: the FP64 pipe at 152 SMs x 2 FP64 lanes
+# per clock x 2070 MHz = 629.3 G FP64 operations/s (the 1.25 TFLOP/s datasheet figure
+# counts an FMA as two); each add or multiply of the site update is one operation.
 FP64_ALU_PEAK_TOPS = 152 * 2 * 2.070e9 / 1e12
 # The kernels also run binary64 additions on the integer ALU pipe (64 lanes per clock
 # per SM, ncu sm__inst_executed_pipe_alu.avg.peak_sustained = 2 warp instructions per
@@ -182,6 +184,23 @@ def _oracle_sample(n: int, sweeps: int):
     return lup / dt / 1e9, dt, lup
 
 
+def _omp_sample(n: int, sweeps: int):
+    """Time the all-core CPU baseline (oracle/stencil_omp.c: Jacobi over planes, pipeline-parallel
+    Gauss-Seidel, the oracle's bits) on the 400^3 grid for `sweeps` sweeps of each smoother.
+    Returns (GLUP/s, seconds, LUP, threads)."""
+    import oracle
+    from paper_1004_1741_gb300 import workloads
+
+    u0 = workloads.laplace_cube(n)
+    oracle.gs_lex_omp(u0[:34, :34, :34].copy(), None, 1.0, 1)  # load the library, start the thread pool
+    t0 = time.perf_counter()
+    oracle.jacobi_omp(u0, None, 1.0, sweeps)
+    oracle.gs_lex_omp(u0, None, 1.0, sweeps)
+    dt = time.perf_counter() - t0
+    lup = 2.0 * sweeps * n ** 3
+    return lup / dt / 1e9, dt, lup, oracle.omp_threads()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -296,22 +315,31 @@ def run_gpu(args):
     flops_per_launch = FP64_OPS_PER_LUP * SWEEPS * N ** 3 / nlaunch
     achieved = flops_per_launch / dur_s / 1e12
     traffic = _traffic_from_profiles(kern)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_COMBINED_PEAK_TOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_COMBINED_PEAK_TOPS, "traffic": traffic, "kernel": kern,
-                "peak_source": "derived: 152 SM x (2 FP64 lanes/clk + 64 integer ALU lanes/clk / %.1f ALU "
-                               "instructions per integer-pipe binary64 add, ncu) x 2070 MHz; achieved counts the 6 "
-                               "algorithmic FP64 operations of a site update (5 adds, 1 multiply)"
-                               % INT_ADD_ALU_INSTR,
-                "frac_of_fp64_pipe_only": achieved / FP64_ALU_PEAK_TOPS}
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # the pipes' peaks measured in this run (throughput probes, after the timed region)
+    probe = measured_peaks(capi, local)
+    fp64_tops = probe["fp64_ops_per_s"] / 1e12
+    comb_tops = (probe["fp64_ops_per_s"] + probe["int_add_f64_per_s"]) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": comb_tops, "unit": "TFLOP/s",
+                "frac": achieved / comb_tops, "traffic": traffic, "kernel": kern,
+                "peak_source": "measured in this run (stencil_probe_throughput): FP64 additions/s %.3e + binary64 "
+                               "additions/s on the integer pipes %.3e, both from independent chains at 32 warps per "
+                               "SM; achieved counts the 6 algorithmic FP64 operations of a site update (5 adds, "
+                               "1 multiply)" % (probe["fp64_ops_per_s"], probe["int_add_f64_per_s"]),
+                "frac_of_fp64_pipe_only": achieved / fp64_tops,
+                "hbm": {"achieved_gbs": 16.0 * SWEEPS * N ** 3 / nlaunch / dur_s / 1e9, "peak_gbs": hbm,
+                        "peak_source": src + " (MEASURED_PEAKS.json copy)",
+                        "frac": 16.0 * SWEEPS * N ** 3 / nlaunch / dur_s / 1e9 / hbm},
+                "derived_peak_unit_counts": FP64_COMBINED_PEAK_TOPS}
     hbm_bound = {str(nt): hbm * nt / 16.0 for nt in NT_SWEEP}
 
     details = {"glups": glups, "hbm_roofline_glups_fp64": hbm_bound, "hbm_gbs": hbm, "hbm_source": src,
-               "fp64_pipe_roofline_glups": FP64_ALU_PEAK_TOPS * 1e12 / FP64_OPS_PER_LUP / 1e9,
-               "fp64_plus_int_roofline_glups": FP64_COMBINED_PEAK_TOPS * 1e12 / FP64_OPS_PER_LUP / 1e9,
+               "probe": probe,
+               "fp64_pipe_roofline_glups": fp64_tops * 1e12 / FP64_OPS_PER_LUP / 1e9,
+               "fp64_plus_int_roofline_glups": comb_tops * 1e12 / FP64_OPS_PER_LUP / 1e9,
                "frac_of_min_roofline": {k: v / min(hbm / 16.0 * HEADLINE[k]["nt"],
-                                                   FP64_COMBINED_PEAK_TOPS * 1e3 / FP64_OPS_PER_LUP)
+                                                   comb_tops * 1e3 / FP64_OPS_PER_LUP)
                                         for k, v in glups.items()}}
 
     # temporal depth sweep (one 100-sweep run per nt and smoother, after the timed region)
@@ -326,12 +354,17 @@ def run_gpu(args):
     if not args.skip_e2e:
         e2e = run_e2e(ctx, capi, torch, u_host, dev, stream, args)
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         g, dt, lup = _oracle_sample(N, 2)
         cpu = {"value": g, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
                "sample": "400^3 FP64, 2 Jacobi + 2 Gauss-Seidel sweeps (%.0f MLUP, %.1f s), serial C oracle"
                          % (lup / 1e6, dt)}
+        g2, dt2, lup2, thr = _omp_sample(N, 8)
+        cpu_all = {"value": g2, "unit": "GLUP/s", "cores": thr, "nproc": os.cpu_count(), "kind": "openmp",
+                   "sample": "400^3 FP64, 8 Jacobi (planes split among threads) + 8 pipeline-parallel Gauss-Seidel "
+                             "sweeps (%.0f MLUP, %.1f s), the oracle's arithmetic on all host cores, bit-exact with "
+                             "it" % (lup2 / 1e6, dt2)}
 
     if rank == 0:
         line = {
@@ -345,7 +378,8 @@ def run_gpu(args):
                        "gs": {"nt": cg["nt"], "tile": list(cg["tile"]), "variant": cg["variant"],
                               "int_adds": cg["int_adds"]}, "parallelism": "replicas" if world > 1 else "1gpu",
                        "l2": "inputs larger than L2 (2 x 512.6 MB vs 129 MB); no flush"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
             "details": details,
         }
         print(json.dumps(line), flush=True)
@@ -353,6 +387,17 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def measured_peaks(capi, device: int) -> dict:
+    """Throughput probes on a context of their own (its workspace, including 2 GiB for the copy probe, is
+    released afterwards): whole-GPU FP64, FP32, integer-ALU and integer-pipe binary64-addition rates and the
+    copy kernel's DRAM bandwidth."""
+    c = capi.Context(device)
+    try:
+        return capi.stencil_probe_throughput(c, copy_bytes=2 << 30)
+    finally:
+        c.close()
 
 
 def launch_counts(ctx, smoother, cfg):

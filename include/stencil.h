@@ -222,10 +222,12 @@ int residual_norm(stencil_ctx* ctx, const double* u, const double* f, const int6
  * STENCIL_F32 (u and f are double* or float* accordingly).  Every grid ends
  * exactly as after stencil_jacobi / stencil_gs_lex with the same arguments.
  * params (may be NULL): nt, tile, b and int_adds shared by all grids
- * (defaults nt = 1; Gauss-Seidel at nt = 1..4: column-march tasks of 8x8
- * columns (16x8 for FP32) x 100 + nt - 1 planes, each task applying its nt
- * sweeps, unless variant is 1..3, else 16^3 tile tasks; Jacobi 32x4 (FP64) or 32x8 (FP32) z-march columns at nt = 1,
- * else 32x8x8 tile tasks; FP64 int_adds: the adaptive form); a must be 0.
+ * (defaults nt = 1; Gauss-Seidel at nt = 1, and at nt = 2..4 without a
+ * tile or with variant 4/5: column-march tasks of 8x8 columns (16x8 for
+ * FP32) x 100 + nt - 1 planes, each task applying its nt sweeps, unless
+ * variant is 1..3; else 16^3 tile tasks; Jacobi 32x4 (FP64) or 32x8 (FP32)
+ * z-march columns at nt = 1, else 32x8x8 tile tasks; FP64 int_adds: the
+ * adaptive form); a must be 0.
  * Jacobi takes a workspace of the total size of the batch, FP64 with f a
  * further one for h^2 f when the budget has room.  Blocking: returns when the
  * batch is done; STENCIL_ERR_TIMEOUT if a bounded device wait expired (the
@@ -370,6 +372,30 @@ void stencil_server_destroy(stencil_server* srv);
  * handled.  Blocking. */
 int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t seed, uint64_t* out_mismatch,
                              uint64_t* out_fast);
+
+/* Throughput probes (not in the paper; they measure the roofline's
+ * denominators on the GPU at hand): whole-GPU rates of FP64 additions (the
+ * smoothers' FMA-form addition, one rounding each), FP32 additions, 32-bit
+ * integer ALU instructions (lop3), binary64 additions carried out on the
+ * integer pipes (the smoothers' ordered integer-pipe addition on operands in
+ * its fast path; int_add_fast_fraction must be 1), each from 8 independent
+ * dependency chains per thread at 32 warps per SM; and, when copy_bytes >= 32,
+ * the DRAM bandwidth of a 16-byte-vector copy kernel over copy_bytes of
+ * workspace (read + write bytes per second).  sm_count and clock_khz are the
+ * device's (cudaDevAttrClockRate: the maximum SM clock).  Blocking; changes
+ * no device setting. */
+typedef struct stencil_probe_result {
+  double fp64_ops_per_s;
+  double fp32_ops_per_s;
+  double alu_ops_per_s;
+  double int_add_f64_per_s;
+  double int_add_fast_fraction;
+  double copy_bytes_per_s;
+  int sm_count;
+  int clock_khz;
+} stencil_probe_result;
+
+int stencil_probe_throughput(stencil_ctx* ctx, size_t copy_bytes, stencil_probe_result* out);
 
 /* residual_norm without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc when they

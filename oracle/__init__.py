@@ -284,3 +284,47 @@ def solve_mixed_mg(u: np.ndarray, f: np.ndarray | None, h: float, smoother: int,
     if rc not in (0, -5):
         raise RuntimeError("oracle_solve_mixed_mg rc=%d" % rc)
     return out, rel.value, its.value, rc == 0
+
+
+# ------------------------------------------------------------------ all-core CPU baseline (OpenMP) --
+_OMP = None
+
+
+def _omp():
+    global _OMP
+    if _OMP is None:
+        lib = ctypes.CDLL(_build.build_omp())
+        lib.omp_jacobi_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _D, _D, _I, _I]
+        lib.omp_gs_lex_f64.argtypes = [_P, _P, _I64, _I64, _I64, _D, _D, _I, _I]
+        lib.omp_jacobi_f64.restype = _I
+        lib.omp_gs_lex_f64.restype = _I
+        lib.omp_max_threads.restype = _I
+        _OMP = lib
+    return _OMP
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP baseline uses by default (all host cores unless OMP_NUM_THREADS says otherwise)."""
+    return int(_omp().omp_max_threads())
+
+
+def jacobi_omp(u: np.ndarray, f: np.ndarray | None = None, h: float = 1.0, nsweeps: int = 1, a: float = 0.0,
+               b: float | None = None, threads: int = 0) -> np.ndarray:
+    """Jacobi sweeps on all host cores (planes split among threads); the oracle's bits.  FP64."""
+    out = np.array(u, copy=True, order="C")
+    _check(out, f, np.float64)
+    rc = _omp().omp_jacobi_f64(_ptr(out), _ptr(f), *_dims(out), h, a, B64 if b is None else b, nsweeps, threads)
+    if rc != 0:
+        raise RuntimeError("omp_jacobi_f64 rc=%d" % rc)
+    return out
+
+
+def gs_lex_omp(u: np.ndarray, f: np.ndarray | None = None, h: float = 1.0, nsweeps: int = 1,
+               b: float | None = None, threads: int = 0) -> np.ndarray:
+    """Pipeline-parallel lexicographic Gauss-Seidel on all host cores (Sec. 3); the oracle's bits.  FP64."""
+    out = np.array(u, copy=True, order="C")
+    _check(out, f, np.float64)
+    rc = _omp().omp_gs_lex_f64(_ptr(out), _ptr(f), *_dims(out), h, B64 if b is None else b, nsweeps, threads)
+    if rc != 0:
+        raise RuntimeError("omp_gs_lex_f64 rc=%d" % rc)
+    return out

@@ -68,6 +68,13 @@ class stencil_server_stats(ctypes.Structure):
                 ("hbm_peak", ctypes.c_size_t), ("queue_depth", ctypes.c_int), ("active", ctypes.c_int)]
 
 
+class stencil_probe_result(ctypes.Structure):
+    _fields_ = [("fp64_ops_per_s", ctypes.c_double), ("fp32_ops_per_s", ctypes.c_double),
+                ("alu_ops_per_s", ctypes.c_double), ("int_add_f64_per_s", ctypes.c_double),
+                ("int_add_fast_fraction", ctypes.c_double), ("copy_bytes_per_s", ctypes.c_double),
+                ("sm_count", ctypes.c_int), ("clock_khz", ctypes.c_int)]
+
+
 STENCIL_PENDING = 1
 STENCIL_REQ_JACOBI = 0
 STENCIL_REQ_GS = 1
@@ -113,6 +120,7 @@ _SIGS = {
                                _P]),
     "stencil_mg_solve": (_I, [_P, _P, _P, _I64P, _D, _I, _I, _I, _I, _I, _D, _I, ctypes.POINTER(_D),
                               ctypes.POINTER(_I), _P]),
+    "stencil_probe_throughput": (_I, [_P, ctypes.c_size_t, ctypes.POINTER(stencil_probe_result)]),
     "stencil_solve_mixed_mg": (_I, [_P, _P, _P, _I64P, _D, _I, _I, _I, _I, _I, _D, _I, _I, ctypes.POINTER(_D),
                                     ctypes.POINTER(_I), _P]),
 }
@@ -339,6 +347,13 @@ def stencil_autotune(ctx: Context, smoother: int, u: torch.Tensor, f: torch.Tens
     _check(ctx, rc)
     return ({"nt": out.nt, "tile": (out.tile_x, out.tile_y, out.tile_z), "variant": out.variant,
              "int_adds": out.int_adds}, g.value)
+
+
+def stencil_probe_throughput(ctx: Context, copy_bytes: int = 0) -> dict:
+    """Measured whole-GPU rates of the pipes the smoothers use (include/stencil.h stencil_probe_throughput)."""
+    out = stencil_probe_result()
+    _check(ctx, load_library().stencil_probe_throughput(ctx.handle, int(copy_bytes), ctypes.byref(out)))
+    return {name: getattr(out, name) for name, _ in stencil_probe_result._fields_}
 
 
 def residual_norm_noalloc(u: torch.Tensor, f: torch.Tensor | None, h: float, r_out: torch.Tensor | None = None,

@@ -24,7 +24,9 @@ static int batched_run(stencil_ctx* ctx, int n, void* const* u, const void* cons
   const int nt = (p && p->nt > 0) ? p->nt : 1;
   // Gauss-Seidel with one to four sweeps per pass runs the column-march tasks unless a tile-task variant is
   // asked for (nt > 1: tasks of nt sweeps, gs_column_ns.cuh)
-  const bool column = smoother == STENCIL_GS && nt <= 4 && (!p || p->variant == 0 || p->variant >= 4);
+  const bool tiled = p && (p->tile_x || p->tile_y || p->tile_z);
+  const bool column = smoother == STENCIL_GS && nt <= 4 &&
+                      (!p || (p->variant == 0 && (nt == 1 || !tiled)) || p->variant >= 4);
   if (column) {
     if (p && p->a != 0.0) return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "weighted sweeps are not batched");
     const int cx = (p && p->tile_x) ? p->tile_x : (sizeof(T) == 8 ? 8 : 16);

@@ -633,3 +633,14 @@ def test_jacobi_inplace_needs_no_second_grid():
     with pytest.raises(capi.StencilError):
         capi.stencil_jacobi(c, _dev(u0), None, 1.0, 2, nt=2, variant=6)
     c.close()
+
+
+def test_throughput_probe(ctx):
+    """The throughput probes report positive whole-GPU rates; the integer-pipe binary64 additions all take
+    the exact fast path; FP32 issues faster than FP64; the copy kernel's bandwidth is a DRAM figure."""
+    r = capi.stencil_probe_throughput(ctx, copy_bytes=1 << 30)
+    assert r["int_add_fast_fraction"] == 1.0
+    assert r["fp64_ops_per_s"] > 1e11 and r["fp32_ops_per_s"] > r["fp64_ops_per_s"]
+    assert r["alu_ops_per_s"] > r["int_add_f64_per_s"] > 0
+    assert 5e11 < r["copy_bytes_per_s"] < 2e13
+    assert r["sm_count"] > 0 and r["clock_khz"] > 0
