@@ -644,3 +644,21 @@ def test_throughput_probe(ctx):
     assert r["alu_ops_per_s"] > r["int_add_f64_per_s"] > 0
     assert 5e11 < r["copy_bytes_per_s"] < 2e13
     assert r["sm_count"] > 0 and r["clock_khz"] > 0
+
+
+@pytest.mark.parametrize("smoother,sweeps", [(capi.STENCIL_JACOBI, 50), (capi.STENCIL_GS, 20)])
+def test_batched_full_config_sampled(ctx, smoother, sweeps):
+    """The full 256-grid batch of uneven Poisson grids (extents multiples of 16 in [32, 192], seed 3) as the
+    benchmark runs it: one batched call with the library defaults, then 16 of the grids (every 16th by size
+    order, smallest to largest) compared with the oracle element by element."""
+    cases = W.batched_poisson(256)
+    us = [_dev(c.u) for c in cases]
+    fs = [_dev(c.f) for c in cases]
+    hs = [c.h for c in cases]
+    capi.stencil_batched(ctx, us, fs, hs, [sweeps] * len(cases), smoother)
+    torch.cuda.synchronize()
+    order = sorted(range(len(cases)), key=lambda i: cases[i].nx * cases[i].ny * cases[i].nz)
+    ofn = oracle.jacobi if smoother == capi.STENCIL_JACOBI else oracle.gs_lex
+    for i in order[::16]:
+        c = cases[i]
+        _assert_exact(us[i].cpu().numpy(), ofn(c.u, c.f, c.h, sweeps), "batched grid %d %s" % (i, (c.nx, c.ny, c.nz)))
