@@ -767,13 +767,16 @@ def run_suite_mg(args):
 
 
 def run_suite_served(args):
-    """Served stream: Poisson arrivals of smoothing and solve requests (sides
-    log-uniform in [32, 384], rounded to multiples of 16; 10-200 sweeps or a solve
-    to 1e-8 capped at 2000 sweeps; FP64/FP32), 150 GB HBM budget, for a range of
-    arrival rates; p50/p99 latency, GLUP/s, admitted/cancelled per rate.  At most
-    --slots requests are admitted at once; at the end of the arrival window the
-    requests never admitted are cancelled (counted) and the admitted ones drain."""
+    """Served stream: Poisson arrivals of smoothing and solve requests (sides log-uniform in [32, 384],
+    rounded to multiples of 16, solve requests one less so that their multigrid levels nest; 10-200 sweeps,
+    or a solve to 1e-8 capped at 2000 fine-grid sweeps; FP64/FP32 smoothing), 150 GB HBM budget, for a range
+    of arrival rates; p50/p99 latency, GLUP/s, admitted/cancelled per rate.  At most --slots requests are on
+    the device at once; at the end of the arrival window the requests never admitted are cancelled (counted)
+    and the admitted ones drain.  Beside it, the same streams served one request at a time through the plain
+    single-grid calls (copy in, smooth or multigrid-solve, copy out), first come first served: the per-request
+    baseline."""
     import numpy as np
+    import torch
 
     from paper_1004_1741_gb300 import capi, workloads
 
@@ -792,9 +795,20 @@ def run_suite_served(args):
             pool[key] = (np.ascontiguousarray(u.astype(dt)), np.ascontiguousarray(fz.astype(dt)))
         return pool[key]
 
-    out = []
-    for rate in rates:
-        reqs = workloads.served_stream(rate, max(1, int(rate * window * 1.2)), seed=5)
+    def shape(r):
+        nn = max(32, min(384, 16 * round(r.n / 16)))
+        if r.kind == "solve":
+            nn -= 1
+        dt = np.float64 if (r.dtype == "f64" or r.kind == "solve") else np.float32
+        return nn, dt
+
+    kinds = {"jacobi": capi.STENCIL_REQ_JACOBI, "gs": capi.STENCIL_REQ_GS, "solve": capi.STENCIL_REQ_SOLVE}
+    outs = {}
+
+    def pct(lat, q):
+        return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None
+
+    def served(reqs):
         with capi.Server(0, hbm_budget_bytes=150 * 10 ** 9, sweeps_per_round=10, max_active=args.slots) as srv:
             t0 = time.perf_counter()
             tickets = []
@@ -804,29 +818,75 @@ def run_suite_served(args):
                 now = time.perf_counter() - t0
                 if r.arrival_s > now:
                     time.sleep(r.arrival_s - now)
-                nn = max(32, min(384, 16 * round(r.n / 16)))
-                dt = np.float64 if (r.dtype == "f64" or r.kind == "solve") else np.float32
+                nn, dt = shape(r)
                 u, fz = inputs(nn, dt)
-                kind = {"jacobi": capi.STENCIL_REQ_JACOBI, "gs": capi.STENCIL_REQ_GS, "solve": capi.STENCIL_REQ_SOLVE}[r.kind]
-                tickets.append(srv.submit(kind, u, fz, 1.0 / (nn + 1), r.sweeps, rtol=r.rtol))
+                # results are read back into one host buffer per shape (what the copy costs, without
+                # holding a buffer per request; the values are not used)
+                outbuf = outs.setdefault((nn, dt), np.empty_like(u))
+                tickets.append(srv.submit(kinds[r.kind], u, fz, 1.0 / (nn + 1), r.sweeps, rtol=r.rtol,
+                                          u_out=outbuf))
             t_arr = time.perf_counter() - t0
-            # end of the window: what was never admitted is cancelled, admitted work drains
-            for t in tickets:
+            for t in tickets:  # end of the window: what was never admitted is cancelled, admitted work drains
                 srv.cancel(t)
             results = [srv.wait(t, args.drain) for t in tickets]
+            t_end = time.perf_counter() - t0
             st = srv.stats()
-        done = [r for r in results if r and r["status"] in (capi.STENCIL_OK, capi.STENCIL_ERR_NOT_CONVERGED)]
         if any(r is None for r in results):
             raise RuntimeError("served requests did not drain within %.0f s" % args.drain)
+        done = [r for r in results if r["status"] in (capi.STENCIL_OK, capi.STENCIL_ERR_NOT_CONVERGED)]
         lat = sorted(r["latency_s"] for r in done)
-        pct = (lambda q: lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None)
-        out.append({"rate_hz": rate, "submitted": len(tickets), "completed": len(done),
-                    "cancelled": sum(1 for r in results if r and r["status"] == capi.STENCIL_ERR_CANCELLED),
-                    "p50_s": pct(0.5), "p99_s": pct(0.99), "glups": st["glups"], "lup": st["lup_total"],
-                    "busy_s": st["busy_s"], "arrival_window_s": t_arr, "hbm_peak_gb": st["hbm_peak"] / 1e9,
-                    "launches": st["launches"]})
-    line = {"suite": "served", "metric": "p50/p99 latency and GLUP/s vs arrival rate (continuous batching)",
-            "unit": "s", "data": "synthetic", "window_s": window, "results": out}
+        return {"submitted": len(tickets), "completed": len(done),
+                "cancelled": sum(1 for r in results if r["status"] == capi.STENCIL_ERR_CANCELLED),
+                "solves_converged": sum(1 for r in results if r["status"] == capi.STENCIL_OK and r["rel_residual"] >= 0),
+                "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "glups_busy": st["glups"],
+                "glups_wall": st["lup_total"] / t_end / 1e9, "lup": st["lup_total"], "busy_s": st["busy_s"],
+                "wall_s": t_end, "arrival_window_s": t_arr, "hbm_peak_gb": st["hbm_peak"] / 1e9,
+                "launches": st["launches"]}
+
+    def plain(reqs):
+        """The same arrivals, one request at a time (FIFO) through the single-grid calls."""
+        ctx = capi.Context(0)
+        dev = torch.device("cuda", 0)
+        t0 = time.perf_counter()
+        lat, lup, n = [], 0.0, 0
+        for r in reqs:
+            if r.arrival_s > window:
+                break
+            now = time.perf_counter() - t0
+            if r.arrival_s > now:
+                time.sleep(r.arrival_s - now)
+            nn, dt = shape(r)
+            uh, fh = inputs(nn, dt)
+            u = torch.from_numpy(uh).to(dev)
+            f = torch.from_numpy(fh).to(dev)
+            h = 1.0 / (nn + 1)
+            if r.kind == "solve":
+                cyc = 0
+                rel, cyc, _ = capi.stencil_mg_solve(ctx, u, f, h, capi.STENCIL_GS, nu1=2, nu2=2, ncoarse=10,
+                                                    rtol=r.rtol, max_cycles=r.sweeps // 4)
+                lup += 4.0 * cyc * nn ** 3
+            else:
+                (capi.stencil_jacobi if r.kind == "jacobi" else capi.stencil_gs_lex)(ctx, u, f, h, r.sweeps)
+                lup += float(r.sweeps) * nn ** 3
+            u.cpu()
+            lat.append(time.perf_counter() - t0 - r.arrival_s)
+            n += 1
+        t_end = time.perf_counter() - t0
+        ctx.close()
+        lat.sort()
+        return {"completed": n, "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "glups_wall": lup / t_end / 1e9,
+                "wall_s": t_end}
+
+    out = []
+    for rate in rates:
+        reqs = workloads.served_stream(rate, max(1, int(rate * window * 1.2)), seed=5)
+        row = {"rate_hz": rate, "served": served(reqs)}
+        if rate <= args.plain_max_rate:
+            row["plain_per_request"] = plain(reqs)
+        out.append(row)
+    line = {"suite": "served", "metric": "p50/p99 latency and GLUP/s vs arrival rate (continuous batching), beside "
+                                         "the same streams served one request at a time",
+            "unit": "s", "data": "synthetic", "window_s": window, "slots": args.slots, "results": out}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -856,7 +916,9 @@ def main():
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--inner", type=int, default=1, help="FP32 V-cycles per outer iteration (--suite mixed)")
     ap.add_argument("--suite", choices=["mixed", "served", "mg"], help="a secondary workload instead of the headline")
-    ap.add_argument("--rates", default="50,100,200,500,1000,2000")
+    ap.add_argument("--rates", default="2,5,10,25,50,100,200,500,2000")
+    ap.add_argument("--plain-max-rate", type=float, default=50.0,
+                    help="--suite served: rates up to this also run the one-request-at-a-time baseline")
     ap.add_argument("--window", type=float, default=3.0)
     ap.add_argument("--drain", type=float, default=60.0)
     ap.add_argument("--slots", type=int, default=32)

@@ -301,20 +301,28 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
 /* ---------------------------------------------------------------------------
  * Continuous-batching server (not in the paper).
  *
- * A worker thread owns one GPU.  Each round it admits waiting requests in
- * arrival order while their device memory fits hbm_budget_bytes (0 = no
- * cap) and fewer than max_active requests are admitted (0 = no slot limit), copies their grids to the device where they stay until completion,
- * runs up to sweeps_per_round sweeps (0 = 10) of every admitted request --
- * all requests of one (smoother, dtype) class in ONE batched persistent
- * launch -- tests solve requests' residuals, and copies finished grids back.
- * Requests that arrive meanwhile join the next round.  A request's result is
- * the same alone and in any mix.
+ * Two worker threads own one GPU.  A copy thread admits waiting requests in
+ * arrival order while their device memory fits hbm_budget_bytes (0 = no cap)
+ * and fewer than max_active requests are admitted (0 = no slot limit), takes
+ * their grids from a stream-ordered memory pool of the server (no cudaMalloc
+ * or cudaFree per request) and copies them to the device on a stream of its
+ * own, where they stay until completion, and copies finished grids back.  A
+ * compute thread runs rounds over the requests on the device: up to
+ * sweeps_per_round sweeps (0 = 10) of every smoothing request -- all requests
+ * of one (smoother, dtype) class in ONE batched persistent launch -- and one
+ * multigrid cycle of every solve request.  Requests that arrive meanwhile are
+ * admitted as memory and slots free up; their copies overlap the rounds'
+ * kernels.  A request's result is the same alone and in any mix.
  * ------------------------------------------------------------------------- */
 #define STENCIL_PENDING 1 /* poll/wait: the request has not finished yet */
 
 #define STENCIL_REQ_JACOBI 0 /* nsweeps Jacobi sweeps */
 #define STENCIL_REQ_GS 1     /* nsweeps Gauss-Seidel sweeps */
-#define STENCIL_REQ_SOLVE 2  /* Gauss-Seidel sweeps until ||f-Au||/||f|| <= rtol, at most nsweeps (FP64 only) */
+#define STENCIL_REQ_SOLVE 2  /* solve until ||f-Au||/||f|| <= rtol (FP64 only): multigrid V(2,2) cycles with the
+                              * Gauss-Seidel smoother (stencil_mg_solve, sweeps_per_round sweeps on the coarsest
+                              * level) when every extent is odd and >= 3, else Gauss-Seidel sweeps; nsweeps caps
+                              * the fine-grid sweeps, a cycle counting 4; the residual is tested after each cycle
+                              * or round of sweeps */
 
 typedef struct stencil_server stencil_server;
 

@@ -1,19 +1,18 @@
 // Continuous-batching server for smoothing and solve requests (not in the
 // paper; it serves the smoothers to many concurrent users of one GPU).
 //
-// A worker thread owns the GPU work.  Each round it (1) admits waiting
-// requests in arrival order while their device memory fits the HBM budget
-// and a slot is free,
-// copying their grids to the device, where they stay until the request
-// completes; (2) runs up to `sweeps_per_round` sweeps of every admitted
-// request, all requests of one (smoother, dtype) class in ONE persistent
-// batched launch (stencil_batched); (3) checks solve requests' residuals;
-// (4) copies finished grids back and frees their memory.  Requests that
-// arrive while a round runs join the next round, as slots and memory free up.
+// Two threads own the GPU work.  The copy thread admits waiting requests in
+// arrival order while their device memory fits the HBM budget and a slot is
+// free, takes their grids from a stream-ordered memory pool and copies them
+// to the device on a copy stream, and hands finished grids back the same way;
+// the compute thread runs rounds over the requests on the device: up to
+// `sweeps_per_round` sweeps of every smoothing request, all requests of one
+// (smoother, dtype) class in ONE persistent batched launch
+// (stencil_batched), and one multigrid V-cycle of every solve request.
+// Copies of requests arriving or leaving overlap the rounds' kernels.
 // A request's result does not depend on the other requests in the mix: the
 // batched kernel is exact per grid, sweeps split into rounds compose exactly,
-// and solve requests test their residual after every `sweeps_per_round`
-// sweeps whatever else is running.
+// and a solve request's cycles and residual tests are its own.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -40,7 +39,9 @@ struct Req {
   void* du = nullptr;
   void* df = nullptr;
   int done_sweeps = 0;
-  int state = 0;  // 0 waiting, 1 active, 2 finished
+  int state = 0;  // 0 waiting, 3 uploading, 1 on the device, 4 finished on the device, 2 reported
+  bool failed = false;
+  double last_rel = -1.0;
   stencil_result res{};
 };
 
@@ -54,13 +55,17 @@ struct stencil_server {
   int quantum = 10;
   int max_active = 0;  // slots: admitted requests at most (0 = memory bound only)
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_work, cv_done, cv_copy;
   std::deque<uint64_t> waiting;
+  std::deque<uint64_t> to_download;
   std::map<uint64_t, Req*> reqs;
   std::vector<uint64_t> active;
+  int admitted_live = 0;  // admitted and not yet handed back
   uint64_t next_ticket = 1;
   bool stop = false;
-  std::thread worker;
+  std::thread worker, copier;
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t cstream = nullptr;
   size_t in_use = 0, peak = 0;
   stencil_server_stats st{};
   std::vector<double> lat;
@@ -89,11 +94,22 @@ static void finish(stencil_server* s, Req* q, int status, double rel) {
   q->state = 2;
 }
 
-// One round of the worker; returns false when there is nothing to do.
-static bool server_round(stencil_server* s) {
-  std::vector<Req*> admit;
+// --- copy thread: admission, uploads, downloads -----------------------------
+//
+// Admits waiting requests in arrival order while their memory fits the budget
+// and a slot is free, takes their grids from the server's stream-ordered
+// memory pool (no cudaMalloc / cudaFree per request) and copies them to the
+// device on the copy stream; hands finished grids back (device -> host) and
+// returns their memory to the pool.  It runs beside the compute thread, so a
+// round's kernels overlap the next requests' copies.
+static bool copy_step(stencil_server* s) {
+  std::vector<Req*> down, admit;
   {
-    std::unique_lock<std::mutex> lk(s->mu);
+    std::lock_guard<std::mutex> lk(s->mu);
+    while (!s->to_download.empty()) {
+      down.push_back(s->reqs[s->to_download.front()]);
+      s->to_download.pop_front();
+    }
     while (!s->waiting.empty()) {
       Req* q = s->reqs[s->waiting.front()];
       if (s->budget && q->bytes > s->budget) {  // can never fit
@@ -104,56 +120,96 @@ static bool server_round(stencil_server* s) {
         continue;
       }
       if (s->budget && s->in_use + q->bytes > s->budget) break;  // wait, in arrival order, for memory
-      if (s->max_active && (int)s->active.size() >= s->max_active) break;  // ... or for a free slot
+      if (s->max_active && s->admitted_live >= s->max_active) break;  // ... or for a free slot
       s->waiting.pop_front();
       s->in_use += q->bytes;
       s->peak = std::max(s->peak, s->in_use);
+      s->admitted_live++;
       q->t_admit = Clock::now();
-      q->state = 1;
+      q->state = 3;
       admit.push_back(q);
-      s->active.push_back(q->ticket);
       s->st.admitted++;
     }
   }
-  stencil_ctx* ctx = s->ctx;
-  cudaStream_t st = ctx->gstream;
-  // upload admitted grids
+  if (down.empty() && admit.empty()) return false;
+  cudaStream_t cs = s->cstream;
+  for (Req* q : down) {
+    const size_t n = (size_t)(q->r.dims[0] + 2) * (size_t)(q->r.dims[1] + 2) * (size_t)(q->r.dims[2] + 2);
+    const size_t esz = q->r.dtype == STENCIL_F64 ? 8 : 4;
+    if (q->r.u_out && q->du && (q->res.status == STENCIL_OK || q->res.status == STENCIL_ERR_NOT_CONVERGED))
+      cudaMemcpyAsync(q->r.u_out, q->du, n * esz, cudaMemcpyDeviceToHost, cs);
+    if (q->du) cudaFreeAsync(q->du, cs);
+    if (q->df) cudaFreeAsync(q->df, cs);
+  }
   for (Req* q : admit) {
     const size_t n = (size_t)(q->r.dims[0] + 2) * (size_t)(q->r.dims[1] + 2) * (size_t)(q->r.dims[2] + 2);
     const size_t esz = q->r.dtype == STENCIL_F64 ? 8 : 4;
-    cudaError_t e = cudaMalloc(&q->du, n * esz);
-    if (e == cudaSuccess && q->r.f_in) e = cudaMalloc(&q->df, n * esz);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->du, q->r.u_in, n * esz, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && q->df) e = cudaMemcpyAsync(q->df, q->r.f_in, n * esz, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMallocFromPoolAsync(&q->du, n * esz, s->pool, cs);
+    if (e == cudaSuccess && q->r.f_in) e = cudaMallocFromPoolAsync(&q->df, n * esz, s->pool, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q->du, q->r.u_in, n * esz, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && q->df) e = cudaMemcpyAsync(q->df, q->r.f_in, n * esz, cudaMemcpyHostToDevice, cs);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      std::lock_guard<std::mutex> lk(s->mu);
-      finish(s, q, STENCIL_ERR_OOM, -1.0);
+      q->failed = true;
     }
   }
+  cudaStreamSynchronize(cs);  // downloads landed, uploads on the device
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (Req* q : down) {
+    q->du = q->df = nullptr;
+    s->in_use -= q->bytes;
+    s->admitted_live--;
+    q->t_done = Clock::now();
+    q->res.latency_s = std::chrono::duration<double>(q->t_done - q->t_submit).count();
+    s->lat.push_back(q->res.latency_s);
+    s->st.completed++;
+    q->state = 2;
+  }
+  for (Req* q : admit) {
+    if (q->failed) {
+      if (q->du) cudaFreeAsync(q->du, cs);
+      if (q->df) cudaFreeAsync(q->df, cs);
+      q->du = q->df = nullptr;
+      s->in_use -= q->bytes;
+      s->admitted_live--;
+      finish(s, q, STENCIL_ERR_OOM, -1.0);
+      q->state = 2;
+      continue;
+    }
+    q->state = 1;
+    s->active.push_back(q->ticket);
+  }
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();
+  return true;
+}
+
+// --- compute thread: one round over the requests on the device --------------
+//
+// Smoothing requests: up to `quantum` sweeps each, all requests of one
+// (smoother, dtype) class in one batched launch.  Solve requests: one
+// multigrid V(2,2) cycle each (lexicographic Gauss-Seidel smoother; plain
+// sweeps when an extent cannot coarsen), residual tested after it.  Requests
+// that finish are handed to the copy thread.
+static bool compute_round(stencil_server* s) {
   std::vector<Req*> act;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    for (uint64_t t : s->active) {
-      Req* q = s->reqs[t];
-      if (q->state == 1) act.push_back(q);
-    }
+    for (uint64_t t : s->active) act.push_back(s->reqs[t]);
   }
-  if (act.empty()) {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->active.clear();
-    return !admit.empty();
-  }
+  if (act.empty()) return false;
+  stencil_ctx* ctx = s->ctx;
+  cudaStream_t st = ctx->gstream;
   const auto t0 = Clock::now();
-  // one batched launch per (smoother, dtype) class
+  double lup = 0.0;
   for (int cls = 0; cls < 4; ++cls) {
     const int smoother = cls / 2 == 0 ? STENCIL_JACOBI : STENCIL_GS;
     const int dtype = cls % 2 == 0 ? STENCIL_F64 : STENCIL_F32;
     std::vector<Req*> grp;
-    for (Req* q : act) {
-      const int sm = q->r.kind == STENCIL_REQ_JACOBI ? STENCIL_JACOBI : STENCIL_GS;
-      if (sm == smoother && q->r.dtype == dtype && q->state == 1) grp.push_back(q);
-    }
+    for (Req* q : act)
+      if (q->r.kind != STENCIL_REQ_SOLVE && q->r.dtype == dtype &&
+          (q->r.kind == STENCIL_REQ_JACOBI ? STENCIL_JACOBI : STENCIL_GS) == smoother)
+        grp.push_back(q);
     if (grp.empty()) continue;
     std::vector<void*> u;
     std::vector<const void*> f;
@@ -167,10 +223,10 @@ static bool server_round(stencil_server* s) {
       h.push_back(q->r.h);
       ns.push_back(std::min(s->quantum, q->r.nsweeps - q->done_sweeps));
     }
-    int rc = stencil_batched(ctx, (int)grp.size(), u.data(), f.data(), dims.data(), h.data(), ns.data(), smoother,
-                             dtype, nullptr, st);
-    s->st.launches++;
+    const int rc = stencil_batched(ctx, (int)grp.size(), u.data(), f.data(), dims.data(), h.data(), ns.data(),
+                                   smoother, dtype, nullptr, st);
     std::lock_guard<std::mutex> lk(s->mu);
+    s->st.launches++;
     for (size_t i = 0; i < grp.size(); ++i) {
       Req* q = grp[i];
       if (rc != STENCIL_OK) {
@@ -178,76 +234,85 @@ static bool server_round(stencil_server* s) {
         continue;
       }
       q->done_sweeps += ns[i];
-      s->lup += (double)q->r.dims[0] * q->r.dims[1] * q->r.dims[2] * ns[i];
+      lup += (double)q->r.dims[0] * q->r.dims[1] * q->r.dims[2] * ns[i];
+      if (q->done_sweeps >= q->r.nsweeps) finish(s, q, STENCIL_OK, -1.0);
     }
   }
-  // solve requests: residual after every round
   for (Req* q : act) {
-    if (q->state != 1) continue;
-    Geom g = make_geom((int)q->r.dims[0], (int)q->r.dims[1], (int)q->r.dims[2]);
-    if (q->r.kind == STENCIL_REQ_SOLVE) {
-      double ab = 0.0, rel = 0.0;
-      int rc = residual_norm(ctx, (const double*)q->du, (const double*)q->df, q->r.dims, q->r.h, nullptr, &ab, &rel,
-                             st);
-      std::lock_guard<std::mutex> lk(s->mu);
-      if (rc != STENCIL_OK)
-        finish(s, q, rc, -1.0);
-      else if (rel <= q->r.rtol)
-        finish(s, q, STENCIL_OK, rel);
-      else if (q->done_sweeps >= q->r.nsweeps)
-        finish(s, q, STENCIL_ERR_NOT_CONVERGED, rel);
-    } else if (q->done_sweeps >= q->r.nsweeps) {
-      std::lock_guard<std::mutex> lk(s->mu);
-      finish(s, q, STENCIL_OK, -1.0);
+    if (q->r.kind != STENCIL_REQ_SOLVE) continue;
+    const bool odd = q->r.dims[0] % 2 && q->r.dims[1] % 2 && q->r.dims[2] % 2 && q->r.dims[0] >= 3 &&
+                     q->r.dims[1] >= 3 && q->r.dims[2] >= 3;
+    const int rem = q->r.nsweeps - q->done_sweeps;
+    // a V(2,2) cycle counts four fine-grid sweeps; one level: min(quantum, rem) sweeps per round
+    const int levels = odd && rem >= 4 ? 32 : 1;
+    const int per = levels > 1 ? 4 : std::min(s->quantum, rem);
+    double rel = -1.0;
+    int cyc = 0;
+    int rc = STENCIL_OK;
+    if (per > 0)
+      rc = stencil_mg_solve(ctx, (double*)q->du, (const double*)q->df, q->r.dims, q->r.h, STENCIL_GS, 2, 2,
+                            levels > 1 ? s->quantum : per, levels, q->r.rtol, 1, &rel, &cyc, st);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (rc != STENCIL_OK && rc != STENCIL_ERR_NOT_CONVERGED) {
+      finish(s, q, rc, -1.0);
+      continue;
     }
-    (void)g;
+    if (per == 0) {  // the cap is spent: the residual after the last round decides
+      finish(s, q, q->last_rel >= 0 && q->last_rel <= q->r.rtol ? STENCIL_OK : STENCIL_ERR_NOT_CONVERGED,
+             q->last_rel);
+      continue;
+    }
+    q->done_sweeps += per * cyc;
+    q->last_rel = rel;
+    lup += (double)q->r.dims[0] * q->r.dims[1] * q->r.dims[2] * per * cyc;
+    if (rel <= q->r.rtol)
+      finish(s, q, STENCIL_OK, rel);
+    else if (q->done_sweeps + (levels > 1 ? 4 : 1) > q->r.nsweeps)
+      finish(s, q, STENCIL_ERR_NOT_CONVERGED, rel);
   }
   cudaStreamSynchronize(st);
+  std::lock_guard<std::mutex> lk(s->mu);
   s->busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
-  // retire finished requests
-  std::vector<Req*> fin;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    std::vector<uint64_t> keep;
-    for (uint64_t t : s->active) {
-      Req* q = s->reqs[t];
-      if (q->state == 2)
-        fin.push_back(q);
-      else
-        keep.push_back(t);
+  s->lup += lup;
+  std::vector<uint64_t> keep;
+  for (uint64_t t : s->active) {
+    Req* q = s->reqs[t];
+    if (q->state == 2) {  // finished on the device: to the copy thread
+      q->state = 4;
+      s->to_download.push_back(t);
+    } else {
+      keep.push_back(t);
     }
-    s->active.swap(keep);
   }
-  for (Req* q : fin) {
-    const size_t n = (size_t)(q->r.dims[0] + 2) * (size_t)(q->r.dims[1] + 2) * (size_t)(q->r.dims[2] + 2);
-    const size_t esz = q->r.dtype == STENCIL_F64 ? 8 : 4;
-    if (q->r.u_out && q->du && (q->res.status == STENCIL_OK || q->res.status == STENCIL_ERR_NOT_CONVERGED))
-      cudaMemcpy(q->r.u_out, q->du, n * esz, cudaMemcpyDeviceToHost);
-    if (q->du) cudaFree(q->du);
-    if (q->df) cudaFree(q->df);
-    q->du = q->df = nullptr;
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->in_use -= q->bytes;
-    q->t_done = Clock::now();
-    q->res.latency_s = std::chrono::duration<double>(q->t_done - q->t_submit).count();
-    s->lat.push_back(q->res.latency_s);
-    s->st.completed++;
-  }
-  if (!fin.empty()) s->cv_done.notify_all();
+  s->active.swap(keep);
+  s->cv_copy.notify_all();
   return true;
 }
 
-static void server_main(stencil_server* s) {
+static void compute_main(stencil_server* s) {
   cudaSetDevice(s->ctx->device);
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait_for(lk, std::chrono::milliseconds(50),
-                          [&] { return s->stop || !s->waiting.empty() || !s->active.empty(); });
+      s->cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->stop || !s->active.empty(); });
       if (s->stop) break;
-      if (s->waiting.empty() && s->active.empty()) continue;
+      if (s->active.empty()) continue;
     }
-    server_round(s);
+    compute_round(s);
+  }
+}
+
+static void copy_main(stencil_server* s) {
+  cudaSetDevice(s->ctx->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_copy.wait_for(lk, std::chrono::milliseconds(20),
+                          [&] { return s->stop || !s->to_download.empty() || !s->waiting.empty(); });
+      if (s->stop) break;
+    }
+    while (copy_step(s)) {
+    }
   }
 }
 
@@ -263,16 +328,37 @@ int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_by
   int rc = stencil_create(&ctx, device, 0);
   if (rc) return rc;
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking);
+  cudaStream_t cs = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  // the requests' grids come from a pool of their own that keeps what it has taken (no release to the
+  // device between requests); the budget is enforced on admission
+  cudaMemPool_t pool = nullptr;
+  if (e == cudaSuccess) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&pool, &props);
+  }
+  if (e == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   if (e != cudaSuccess) {
+    if (pool) cudaMemPoolDestroy(pool);
+    if (cs) cudaStreamDestroy(cs);
     stencil_destroy(ctx);
-    return set_err(nullptr, STENCIL_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    return set_err(nullptr, STENCIL_ERR_CUDA, "server set-up: %s", cudaGetErrorString(e));
   }
   stencil_server* s = new stencil_server();
   s->ctx = ctx;
   s->budget = hbm_budget_bytes;
   s->quantum = sweeps_per_round > 0 ? sweeps_per_round : 10;
   s->max_active = max_active;
-  s->worker = std::thread(server_main, s);
+  s->pool = pool;
+  s->cstream = cs;
+  s->worker = std::thread(compute_main, s);
+  s->copier = std::thread(copy_main, s);
   *out = s;
   return STENCIL_OK;
 }
@@ -298,7 +384,7 @@ int stencil_server_submit(stencil_server* s, const stencil_request* r, uint64_t*
     s->st.submitted++;
     *ticket = q->ticket;
   }
-  s->cv_work.notify_one();
+  s->cv_copy.notify_one();
   return STENCIL_OK;
 }
 
@@ -360,7 +446,7 @@ int stencil_server_stats_get(stencil_server* s, stencil_server_stats* out) {
   out->hbm_in_use = s->in_use;
   out->hbm_peak = s->peak;
   out->queue_depth = (int)s->waiting.size();
-  out->active = (int)s->active.size();
+  out->active = s->admitted_live;
   return STENCIL_OK;
 }
 
@@ -371,14 +457,19 @@ void stencil_server_destroy(stencil_server* s) {
     s->stop = true;
   }
   s->cv_work.notify_all();
+  s->cv_copy.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  if (s->copier.joinable()) s->copier.join();
   cudaSetDevice(s->ctx->device);
   for (auto& kv : s->reqs) {
     Req* q = kv.second;
-    if (q->du) cudaFree(q->du);
-    if (q->df) cudaFree(q->df);
+    if (q->du) cudaFreeAsync(q->du, s->cstream);
+    if (q->df) cudaFreeAsync(q->df, s->cstream);
     delete q;
   }
+  cudaStreamSynchronize(s->cstream);
+  cudaStreamDestroy(s->cstream);
+  cudaMemPoolDestroy(s->pool);
   stencil_destroy(s->ctx);
   delete s;
 }

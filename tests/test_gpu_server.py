@@ -102,3 +102,45 @@ def test_slot_limit_keeps_results_exact():
             assert srv.wait(t, 60)["status"] == capi.STENCIL_OK
     for r, o in zip(reqs, outs):
         assert np.array_equal(o, _oracle(r))
+
+
+def test_solve_request_runs_multigrid_cycles():
+    """A solve request on odd extents runs multigrid V(2,2) cycles (one per round, residual after each):
+    the result equals the oracle's multigrid solve with the same stopping test, bit for bit, four sweeps
+    counted per cycle; the same request capped before convergence reports its residual."""
+    p = W.sine_modes_problem(31, seed=4)
+    u0 = np.zeros_like(p.f)
+    with capi.Server(0, sweeps_per_round=10) as srv:
+        out = np.empty_like(u0)
+        res = srv.wait(srv.submit(capi.STENCIL_REQ_SOLVE, u0, p.f, p.h, 400, rtol=1e-8, u_out=out), 120)
+        assert res["status"] == capi.STENCIL_OK and res["rel_residual"] <= 1e-8
+        cycles = res["sweeps_done"] // 4
+        assert res["sweeps_done"] == 4 * cycles and 3 <= cycles <= 15
+        ref, rel, rc, ok = oracle.mg_solve(u0, p.f, p.h, oracle.MG_GS, 2, 2, 10, 32, 1e-8, cycles)
+        assert ok and rc == cycles
+        assert np.array_equal(out, ref)
+        out2 = np.empty_like(u0)
+        res2 = srv.wait(srv.submit(capi.STENCIL_REQ_SOLVE, u0, p.f, p.h, 9, rtol=1e-8, u_out=out2), 60)
+        assert res2["status"] == capi.STENCIL_ERR_NOT_CONVERGED and res2["sweeps_done"] == 8
+        ref2, _, _, _ = oracle.mg_solve(u0, p.f, p.h, oracle.MG_GS, 2, 2, 10, 32, 1e-8, 2)
+        assert np.array_equal(out2, ref2)
+
+
+def test_many_requests_overlap_copies_and_rounds():
+    """Forty requests of mixed kinds submitted at once through a four-slot server: copies and rounds
+    interleave (admission keeps at most four on the device), every result equals the oracle, and the pool
+    returns all memory."""
+    reqs = []
+    for i in range(40):
+        kind = (capi.STENCIL_REQ_JACOBI, capi.STENCIL_REQ_GS)[i % 2]
+        reqs.append(_req(kind, (20 + i % 7, 18, 11 + i % 5), 100 + i, dtype=(np.float64, np.float32)[i % 3 == 0],
+                         sweeps=3 + i % 6))
+    with capi.Server(0, sweeps_per_round=4, max_active=4) as srv:
+        outs = [np.empty_like(r["u"]) for r in reqs]
+        ts = [srv.submit(r["kind"], r["u"], r["f"], r["h"], r["nsweeps"], u_out=o) for r, o in zip(reqs, outs)]
+        for t in ts:
+            assert srv.wait(t, 120)["status"] == capi.STENCIL_OK
+        st = srv.stats()
+        assert st["hbm_in_use"] == 0 and st["completed"] == 40 and st["active"] == 0
+    for r, o in zip(reqs, outs):
+        assert np.array_equal(o, _oracle(r))
