@@ -809,7 +809,8 @@ def run_suite_served(args):
         return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None
 
     def served(reqs):
-        with capi.Server(0, hbm_budget_bytes=150 * 10 ** 9, sweeps_per_round=10, max_active=args.slots) as srv:
+        with capi.Server(0, hbm_budget_bytes=150 * 10 ** 9, sweeps_per_round=args.quantum,
+                         max_active=args.slots) as srv:
             t0 = time.perf_counter()
             tickets = []
             for r in reqs:
@@ -862,7 +863,7 @@ def run_suite_served(args):
             h = 1.0 / (nn + 1)
             if r.kind == "solve":
                 cyc = 0
-                rel, cyc, _ = capi.stencil_mg_solve(ctx, u, f, h, capi.STENCIL_GS, nu1=2, nu2=2, ncoarse=10,
+                rel, cyc, _ = capi.stencil_mg_solve(ctx, u, f, h, capi.STENCIL_GS, nu1=2, nu2=2, ncoarse=args.quantum,
                                                     rtol=r.rtol, max_cycles=r.sweeps // 4)
                 lup += 4.0 * cyc * nn ** 3
             else:
@@ -886,7 +887,8 @@ def run_suite_served(args):
         out.append(row)
     line = {"suite": "served", "metric": "p50/p99 latency and GLUP/s vs arrival rate (continuous batching), beside "
                                          "the same streams served one request at a time",
-            "unit": "s", "data": "synthetic", "window_s": window, "slots": args.slots, "results": out}
+            "unit": "s", "data": "synthetic", "window_s": window, "slots": args.slots,
+            "sweeps_per_round": args.quantum, "results": out}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -922,6 +924,7 @@ def main():
     ap.add_argument("--window", type=float, default=3.0)
     ap.add_argument("--drain", type=float, default=60.0)
     ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--quantum", type=int, default=10, help="--suite served: sweeps per request and round")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

@@ -93,8 +93,9 @@ static int df_launch(stencil_ctx* ctx, const DFRun& run, const SiteTable& tb, cu
   return STENCIL_OK;
 }
 
-// A plan: the task queue of one batch shape, resident on the device, plus the
-// CUDA graph that resets the flags and runs the persistent kernel.  The grid
+// A plan: the task queue of one batch shape, resident on the device (taken
+// from the stream-ordered allocator), plus, once the shape recurs, the CUDA
+// graph that resets the flags and runs the persistent kernel.  The grid
 // descriptors (pointers, coefficients) are re-uploaded on every call, so the
 // same plan and graph serve any grids of the same shapes.
 struct DFPlan {
@@ -109,6 +110,7 @@ struct DFPlan {
   DFRun run{};
   cudaGraphExec_t exec = nullptr;
   unsigned long long last_use = 0;
+  unsigned long long uses = 0;  // calls made with this plan
 };
 
 static std::vector<DFPlan*>& plans_of(stencil_ctx* ctx) {
@@ -119,7 +121,7 @@ static std::vector<DFPlan*>& plans_of(stencil_ctx* ctx) {
 static void plan_free(stencil_ctx* ctx, DFPlan* pl) {
   if (pl->exec) cudaGraphExecDestroy(pl->exec);
   if (pl->dev) {
-    cudaFree(pl->dev);
+    cudaFreeAsync(pl->dev, ctx->gstream);  // the plan's work on that stream has completed (its calls block)
     ctx->held -= pl->bytes;
   }
   delete pl;
@@ -175,7 +177,7 @@ static int plan_build(stencil_ctx* ctx, DFPlan* pl, int kind, int n, const Geom*
   if (ctx->budget && ctx->held + pl->bytes > ctx->budget)
     return set_err(ctx, STENCIL_ERR_OOM, "task queue needs %zu bytes; %zu held, budget %zu", pl->bytes, ctx->held,
                    ctx->budget);
-  cudaError_t e = cudaMalloc(&pl->dev, pl->bytes);
+  cudaError_t e = cudaMallocAsync(&pl->dev, pl->bytes, st);  // stream-ordered: no device-wide synchronisation
   if (e != cudaSuccess) {
     cudaGetLastError();
     pl->dev = nullptr;
@@ -198,11 +200,14 @@ static int plan_build(stencil_ctx* ctx, DFPlan* pl, int kind, int n, const Geom*
   return STENCIL_OK;
 }
 
+// The plan's launch: reset the flags and counters, run the persistent kernel.  capture: record it into
+// the plan's CUDA graph (replayed by later calls of the same shape); otherwise launch it directly on the
+// context's graph stream (a plan's first call: shapes that never recur pay no capture).
 template <typename T>
 static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, int D, int nt, const SiteTable& tb,
-                        int int_adds, bool any_f, bool pre_f) {
+                        int int_adds, bool any_f, bool pre_f, bool capture = true) {
   cudaStream_t gs = ctx->gstream;
-  cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e = capture ? cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) : cudaSuccess;
   if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamBeginCapture");
   int rc = STENCIL_OK;
   e = cudaMemsetAsync(pl->dev + pl->b_desc + pl->b_task, 0, pl->b_flag + 256, gs);
@@ -219,6 +224,13 @@ static int plan_capture(stencil_ctx* ctx, DFPlan* pl, int kind, int W, int H, in
     DF_TILE(8, 8, 8)
     DF_TILE(32, 16, 16)
 #undef DF_TILE
+  }
+  if (!capture) {
+    if (e != cudaSuccess) return cuda_err(ctx, e, "flag reset");
+    if (rc == STENCIL_UNSUPPORTED_TILE)
+      return set_err(ctx, STENCIL_ERR_UNSUPPORTED, "dataflow tile %dx%dx%d (supported 16^3, 32x8x8, 8^3, 32x16x16)",
+                     W, H, D);
+    return rc;
   }
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(gs, &graph);
@@ -302,15 +314,23 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
   }
   pl->run.timeout_ns = timeout_ns;
   pl->run.poison = poison;
+  // a plan is captured into a graph at its first call and replayed; with ctx->df_direct_first (the
+  // server, whose batch shapes rarely recur) its first call launches directly and a second call captures
+  bool direct = false;
   if (!pl->exec || pl->exec_timeout != timeout_ns || pl->exec_poison != poison || pl->exec_tb != tb.coords) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     pl->exec = nullptr;
-    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, nt, tb, int_adds, any_f, pre_f);
-    if (rc) return rc;
-    pl->exec_timeout = timeout_ns;
-    pl->exec_poison = poison;
-    pl->exec_tb = tb.coords;
+    if (pl->uses == 0 && ctx->df_direct_first) {
+      direct = true;
+    } else {
+      int rc = plan_capture<T>(ctx, pl, kind, W, H, D, nt, tb, int_adds, any_f, pre_f);
+      if (rc) return rc;
+      pl->exec_timeout = timeout_ns;
+      pl->exec_poison = poison;
+      pl->exec_tb = tb.coords;
+    }
   }
+  pl->uses++;
   // ---- descriptors of this call's grids
   std::vector<DFGridDesc> gd((size_t)n);
   long long fbase = 0;
@@ -332,12 +352,18 @@ int dataflow_run(stencil_ctx* ctx, int kind, int n, T* const* a, T* const* b, co
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->gstream, ctx->ev, 0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(pl->dev, gd.data(), (size_t)n * sizeof(DFGridDesc), cudaMemcpyHostToDevice, ctx->gstream);
-  if (e == cudaSuccess) e = cudaGraphLaunch(pl->exec, ctx->gstream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "dataflow descriptors");
+  if (direct) {
+    int rc = plan_capture<T>(ctx, pl, kind, W, H, D, nt, tb, int_adds, any_f, pre_f, false);
+    if (rc) return rc;
+  } else {
+    e = cudaGraphLaunch(pl->exec, ctx->gstream);
+    ctx->launches++;
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ctx->pinned, pl->run.error, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->gstream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->gstream);
   if (e != cudaSuccess) return cuda_err(ctx, e, "dataflow run");
-  ctx->launches++;
   const int* hs = (const int*)ctx->pinned;
   if (hs[0] != 0)
     return set_err(ctx, STENCIL_ERR_TIMEOUT, "dataflow wait timed out (queue index %d of %lld)", hs[1], pl->ntasks);

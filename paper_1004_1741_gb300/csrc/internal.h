@@ -63,6 +63,7 @@ struct stencil_ctx {
   void* df_plans = nullptr;                 // cached dataflow plans (dataflow.cu)
   unsigned long long df_clock = 0;
   cudaStream_t gstream = nullptr;           // stream for graph capture and replay
+  bool df_direct_first = false;             // dataflow plans: launch a shape's first call without a graph
   cudaEvent_t ev = nullptr;
 };
 

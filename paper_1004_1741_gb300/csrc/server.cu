@@ -350,6 +350,7 @@ int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_by
     stencil_destroy(ctx);
     return set_err(nullptr, STENCIL_ERR_CUDA, "server set-up: %s", cudaGetErrorString(e));
   }
+  ctx->df_direct_first = true;  // a round's batch shape rarely recurs: no graph capture for one-off shapes
   stencil_server* s = new stencil_server();
   s->ctx = ctx;
   s->budget = hbm_budget_bytes;
