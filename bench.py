@@ -840,6 +840,8 @@ def run_suite_served(args):
                 "cancelled": sum(1 for r in results if r["status"] == capi.STENCIL_ERR_CANCELLED),
                 "solves_converged": sum(1 for r in results if r["status"] == capi.STENCIL_OK and r["rel_residual"] >= 0),
                 "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "glups_busy": st["glups"],
+                "smoothing_glups": st["smooth_lup"] / st["smooth_s"] / 1e9 if st["smooth_s"] > 0 else None,
+                "solve_cycles": st["solve_cycles"], "solve_s": st["solve_s"], "smoothing_s": st["smooth_s"],
                 "glups_wall": st["lup_total"] / t_end / 1e9, "lup": st["lup_total"], "busy_s": st["busy_s"],
                 "wall_s": t_end, "arrival_window_s": t_arr, "hbm_peak_gb": st["hbm_peak"] / 1e9,
                 "launches": st["launches"]}
@@ -850,6 +852,7 @@ def run_suite_served(args):
         dev = torch.device("cuda", 0)
         t0 = time.perf_counter()
         lat, lup, n = [], 0.0, 0
+        t_smooth, lup_smooth = 0.0, 0.0
         for r in reqs:
             if r.arrival_s > window:
                 break
@@ -867,8 +870,13 @@ def run_suite_served(args):
                                                     rtol=r.rtol, max_cycles=r.sweeps // 4)
                 lup += 4.0 * cyc * nn ** 3
             else:
+                torch.cuda.synchronize()
+                ts = time.perf_counter()
                 (capi.stencil_jacobi if r.kind == "jacobi" else capi.stencil_gs_lex)(ctx, u, f, h, r.sweeps)
+                torch.cuda.synchronize()
+                t_smooth += time.perf_counter() - ts
                 lup += float(r.sweeps) * nn ** 3
+                lup_smooth += float(r.sweeps) * nn ** 3
             u.cpu()
             lat.append(time.perf_counter() - t0 - r.arrival_s)
             n += 1
@@ -876,7 +884,7 @@ def run_suite_served(args):
         ctx.close()
         lat.sort()
         return {"completed": n, "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "glups_wall": lup / t_end / 1e9,
-                "wall_s": t_end}
+                "smoothing_glups": lup_smooth / t_smooth / 1e9 if t_smooth > 0 else None, "wall_s": t_end}
 
     out = []
     for rate in rates:

@@ -354,6 +354,8 @@ typedef struct stencil_server_stats {
   double glups;                /* lup_total / busy_s / 1e9 */
   size_t hbm_in_use, hbm_peak; /* request memory on the device */
   int queue_depth, active;
+  double smooth_lup, smooth_s; /* smoothing requests: updates and seconds of their batched launches */
+  double solve_cycles, solve_s; /* solve requests: multigrid cycles (or rounds of sweeps) and their seconds */
 } stencil_server_stats;
 
 int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_bytes, int sweeps_per_round,

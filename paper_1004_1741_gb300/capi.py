@@ -65,7 +65,9 @@ class stencil_server_stats(ctypes.Structure):
                 ("cancelled", ctypes.c_uint64), ("launches", ctypes.c_uint64), ("p50_s", ctypes.c_double),
                 ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double), ("lup_total", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("glups", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t),
-                ("hbm_peak", ctypes.c_size_t), ("queue_depth", ctypes.c_int), ("active", ctypes.c_int)]
+                ("hbm_peak", ctypes.c_size_t), ("queue_depth", ctypes.c_int), ("active", ctypes.c_int),
+                ("smooth_lup", ctypes.c_double), ("smooth_s", ctypes.c_double), ("solve_cycles", ctypes.c_double),
+                ("solve_s", ctypes.c_double)]
 
 
 class stencil_probe_result(ctypes.Structure):

@@ -201,7 +201,7 @@ static bool compute_round(stencil_server* s) {
   stencil_ctx* ctx = s->ctx;
   cudaStream_t st = ctx->gstream;
   const auto t0 = Clock::now();
-  double lup = 0.0;
+  double lup = 0.0, smooth_lup = 0.0, cycles = 0.0;
   for (int cls = 0; cls < 4; ++cls) {
     const int smoother = cls / 2 == 0 ? STENCIL_JACOBI : STENCIL_GS;
     const int dtype = cls % 2 == 0 ? STENCIL_F64 : STENCIL_F32;
@@ -238,6 +238,9 @@ static bool compute_round(stencil_server* s) {
       if (q->done_sweeps >= q->r.nsweeps) finish(s, q, STENCIL_OK, -1.0);
     }
   }
+  cudaStreamSynchronize(st);
+  const auto t1 = Clock::now();
+  smooth_lup = lup;
   for (Req* q : act) {
     if (q->r.kind != STENCIL_REQ_SOLVE) continue;
     const bool odd = q->r.dims[0] % 2 && q->r.dims[1] % 2 && q->r.dims[2] % 2 && q->r.dims[0] >= 3 &&
@@ -264,6 +267,7 @@ static bool compute_round(stencil_server* s) {
     }
     q->done_sweeps += per * cyc;
     q->last_rel = rel;
+    cycles += cyc;
     lup += (double)q->r.dims[0] * q->r.dims[1] * q->r.dims[2] * per * cyc;
     if (rel <= q->r.rtol)
       finish(s, q, STENCIL_OK, rel);
@@ -272,8 +276,13 @@ static bool compute_round(stencil_server* s) {
   }
   cudaStreamSynchronize(st);
   std::lock_guard<std::mutex> lk(s->mu);
-  s->busy_s += std::chrono::duration<double>(Clock::now() - t0).count();
+  const auto t2 = Clock::now();
+  s->busy_s += std::chrono::duration<double>(t2 - t0).count();
   s->lup += lup;
+  s->st.smooth_lup += smooth_lup;
+  s->st.smooth_s += std::chrono::duration<double>(t1 - t0).count();
+  s->st.solve_cycles += cycles;
+  s->st.solve_s += std::chrono::duration<double>(t2 - t1).count();
   std::vector<uint64_t> keep;
   for (uint64_t t : s->active) {
     Req* q = s->reqs[t];
