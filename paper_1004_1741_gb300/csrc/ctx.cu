@@ -146,6 +146,8 @@ void stencil_destroy(stencil_ctx* ctx) {
   dataflow_release(ctx);
   for (auto& s : ctx->slots)
     if (s.ptr) cudaFree(s.ptr);
+  for (auto& en : ctx->slices)
+    if (en.dev) cudaFree(en.dev);
   if (ctx->ev) cudaEventDestroy(ctx->ev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   delete ctx;

@@ -152,9 +152,18 @@ TileGeom make_tile_geom(const Geom& g, int W, int H, int D, int nt, int nsweeps)
 }
 
 // Slices: all tiles (I, J, K) grouped by sigma = I+J+K; cached per (NI, NJ, NK).
+// Slices: all tiles (I, J, K) grouped by sigma = I+J+K; one table per (NI, NJ, NK), the 32 most recently
+// used kept on the device, so that calls alternating between shapes (the levels of a multigrid cycle)
+// upload each table once.
 int ensure_slices(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
-  if (ctx->gs_key[0] == tg.NI && ctx->gs_key[1] == tg.NJ && ctx->gs_key[2] == tg.NK && ctx->slots[SLOT_GS_SLICES].ptr)
-    return STENCIL_OK;
+  for (size_t i = 0; i < ctx->slices.size(); ++i) {
+    SliceEntry& en = ctx->slices[i];
+    if (en.NI == tg.NI && en.NJ == tg.NJ && en.NK == tg.NK) {
+      en.last_use = ++ctx->slice_clock;
+      ctx->slice_cur = (int)i;
+      return STENCIL_OK;
+    }
+  }
   const int nsig = tg.sigma_max + 1;
   std::vector<int> off(nsig + 1, 0);
   for (int K = 0; K < tg.NK; ++K)
@@ -167,24 +176,54 @@ int ensure_slices(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
     for (int J = 0; J < tg.NJ; ++J)
       for (int I = 0; I < tg.NI; ++I) tiles[(size_t)fill[I + J + K]++] = pack_tile(I, J, K);
   const size_t bytes = tiles.size() * sizeof(uint64_t) + off.size() * sizeof(int) + 64;
-  int status;
-  unsigned char* d = (unsigned char*)ws_get(ctx, SLOT_GS_SLICES, bytes, &status);
-  if (!d) return status;
-  cudaError_t e = cudaMemcpyAsync(d, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
+  // room: evict the least recently used table when 32 are held
+  if (ctx->slices.size() >= 32) {
+    size_t lru = 0;
+    for (size_t i = 1; i < ctx->slices.size(); ++i)
+      if (ctx->slices[i].last_use < ctx->slices[lru].last_use) lru = i;
+    cudaError_t e0 = cudaStreamSynchronize(st);  // launches of this stream may still read it
+    if (e0 != cudaSuccess) return cuda_err(ctx, e0, "slice table eviction");
+    cudaFree(ctx->slices[lru].dev);
+    ctx->held -= ctx->slices[lru].bytes;
+    ctx->slices.erase(ctx->slices.begin() + (long)lru);
+  }
+  if (ctx->budget && ctx->held + bytes > ctx->budget)
+    return set_err(ctx, STENCIL_ERR_OOM, "tile-slice table needs %zu bytes; %zu held, budget %zu", bytes, ctx->held,
+                   ctx->budget);
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, STENCIL_ERR_OOM, "cudaMalloc(%zu) for a tile-slice table: %s", bytes, cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(d, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d + tiles.size() * sizeof(uint64_t), off.data(), off.size() * sizeof(int),
+    e = cudaMemcpyAsync((unsigned char*)d + tiles.size() * sizeof(uint64_t), off.data(), off.size() * sizeof(int),
                         cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
-  if (e != cudaSuccess) return cuda_err(ctx, e, "upload of tile slices");
-  ctx->gs_key[0] = tg.NI; ctx->gs_key[1] = tg.NJ; ctx->gs_key[2] = tg.NK;
-  ctx->gs_slice_off = off;
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_err(ctx, e, "upload of tile slices");
+  }
+  SliceEntry en;
+  en.NI = tg.NI;
+  en.NJ = tg.NJ;
+  en.NK = tg.NK;
+  en.dev = d;
+  en.bytes = bytes;
+  en.off = std::move(off);
+  en.last_use = ++ctx->slice_clock;
+  ctx->held += bytes;
+  ctx->slices.push_back(std::move(en));
+  ctx->slice_cur = (int)ctx->slices.size() - 1;
   return STENCIL_OK;
 }
 
-const uint64_t* slices_ptr(stencil_ctx* ctx) { return (const uint64_t*)ctx->slots[SLOT_GS_SLICES].ptr; }
+const uint64_t* slices_ptr(stencil_ctx* ctx) { return (const uint64_t*)ctx->slices[(size_t)ctx->slice_cur].dev; }
 const int* slice_off_ptr(stencil_ctx* ctx) {
-  size_t ntiles = (size_t)ctx->gs_slice_off.back();
-  return (const int*)((const unsigned char*)ctx->slots[SLOT_GS_SLICES].ptr + ntiles * sizeof(uint64_t));
+  const SliceEntry& en = ctx->slices[(size_t)ctx->slice_cur];
+  const size_t ntiles = (size_t)en.off.back();
+  return (const int*)((const unsigned char*)en.dev + ntiles * sizeof(uint64_t));
 }
 
 // Number of tasks of level L.
@@ -193,7 +232,7 @@ int tasks_at_level(const stencil_ctx* ctx, const TileGeom& tg, int L) {
   for (int p = std::min(tg.npass - 1, L / tg.cstride); p >= 0; --p) {
     int sigma = L - tg.cstride * p;
     if (sigma > tg.sigma_max) break;
-    n += ctx->gs_slice_off[sigma + 1] - ctx->gs_slice_off[sigma];
+    n += ctx->slices[(size_t)ctx->slice_cur].off[sigma + 1] - ctx->slices[(size_t)ctx->slice_cur].off[sigma];
   }
   return n;
 }

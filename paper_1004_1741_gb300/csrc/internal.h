@@ -45,15 +45,30 @@ enum SlotId {
 
 }  // namespace stn
 
+namespace stn {
+// One tile-slice table (tiles (I,J,K) grouped by I+J+K) on the device, for one tile-count shape.
+struct SliceEntry {
+  int NI = 0, NJ = 0, NK = 0;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  std::vector<int> off;  // host copy of the prefix offsets
+  unsigned long long last_use = 0;
+};
+}  // namespace stn
+
 struct stencil_ctx {
   int device = 0;
   size_t budget = 0;  // 0 = unlimited
   size_t held = 0;
   std::string err;
   stn::Slot slots[stn::SLOT_COUNT];
-  // Gauss-Seidel geometry cache key of what SLOT_GS_SLICES / SLOT_GS_SITES hold
+  // Gauss-Seidel geometry cache key of what SLOT_GS_SITES holds (entries 3..7)
   int64_t gs_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  std::vector<int> gs_slice_off;  // host copy of the slice prefix offsets
+  // tile-slice tables of the recently used tile-count shapes (the levels of a multigrid cycle each have
+  // their own); `slice_cur` is the one ensure_slices made current
+  std::vector<stn::SliceEntry> slices;
+  int slice_cur = -1;
+  unsigned long long slice_clock = 0;
   int64_t goff_key[6] = {0, 0, 0, 0, 0, 0};  // (W, H, D, nt, sx, sy) of SLOT_GS_GOFF
   int sm_count = 0;
   unsigned long long launches = 0;  // kernels this context has launched
