@@ -643,7 +643,7 @@ def run_suite_mixed(args):
     prob = workloads.sine_modes_problem(nmg, seed=4)
     f = torch.from_numpy(prob.f).to(dev)
     mg = {}
-    for name, sm in (("gs", capi.STENCIL_GS), ("jacobi", capi.STENCIL_JACOBI)):
+    for name, sm in (("gs", capi.STENCIL_GS), ("jacobi", capi.STENCIL_JACOBI), ("gs_rb", capi.STENCIL_GS_RB)):
         def run_f64(u):
             return capi.stencil_mg_solve(ctx, u, f, prob.h, sm, nu1=2, nu2=2, ncoarse=20, rtol=rtol, max_cycles=60)
 
@@ -728,7 +728,7 @@ def run_suite_mg(args):
     ctx = capi.Context(0)
     f = torch.from_numpy(prob.f).to(dev)
     res = {}
-    for name, sm in (("gs", capi.STENCIL_GS), ("jacobi", capi.STENCIL_JACOBI)):
+    for name, sm in (("gs", capi.STENCIL_GS), ("jacobi", capi.STENCIL_JACOBI), ("gs_rb", capi.STENCIL_GS_RB)):
         u = torch.zeros_like(f)
         capi.stencil_mg_solve(ctx, u, f, prob.h, sm, rtol=0.0, max_cycles=1)  # warm (workspace, tables)
         u.zero_()
@@ -739,6 +739,10 @@ def run_suite_mg(args):
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         abs_r, rel_check = capi.residual_norm(ctx, u, f, prob.h)
+        res[name] = {"cycles": cycles, "rel": rel, "reached": ok, "s": t, "s_per_cycle": t / max(cycles, 1),
+                     "rel_check": rel_check, "fine_sweep_equivalent_glups": n ** 3 * 4 * cycles / t / 1e9}
+        if sm == capi.STENCIL_GS_RB:
+            continue
         # plain sweeps of the same smoother for comparison (measured rate, projected count)
         u2 = torch.zeros_like(f)
         rel200, sw, _ = capi.stencil_solve_f64(ctx, u2, f, prob.h, sm, 0.0, 200, 100)
@@ -748,11 +752,7 @@ def run_suite_mg(args):
         rel200, sw, _ = capi.stencil_solve_f64(ctx, u2, f, prob.h, sm, 0.0, 200, 100)
         torch.cuda.synchronize()
         t_sw = time.perf_counter() - t1
-        res[name] = {"cycles": cycles, "rel": rel, "reached": ok, "s": t, "s_per_cycle": t / max(cycles, 1),
-                     "rel_check": rel_check,
-                     "fine_sweep_equivalent_glups": n ** 3 * 4 * cycles / t / 1e9,
-                     "plain_sweeps": {"sweeps": sw, "rel_after": rel200, "s": t_sw,
-                                      "glups": n ** 3 * sw / t_sw / 1e9}}
+        res[name]["plain_sweeps"] = {"sweeps": sw, "rel_after": rel200, "s": t_sw, "glups": n ** 3 * sw / t_sw / 1e9}
     # CPU oracle: one V-cycle on a 127^3 sample of the same problem family
     small = workloads.sine_modes_problem(127, seed=4)
     t0 = time.perf_counter()

@@ -69,6 +69,7 @@ extern "C" {
 
 #define STENCIL_JACOBI 0
 #define STENCIL_GS 1
+#define STENCIL_GS_RB 2 /* red-black Gauss-Seidel: multigrid smoother only */
 
 #define STENCIL_F64 0
 #define STENCIL_F32 1
@@ -249,7 +250,8 @@ int stencil_batched(stencil_ctx* ctx, int n, void* const* u, const void* const* 
  *    trilinear prolongation added to u (x, then y, then z), nu2 sweeps;
  *    ncoarse sweeps on the coarsest level.
  *  smoother: STENCIL_JACOBI = weighted Jacobi, omega = 6/7 (a = b = 1/7);
- *    STENCIL_GS = lexicographic Gauss-Seidel (b = 1/6).
+ *    STENCIL_GS = lexicographic Gauss-Seidel (b = 1/6); STENCIL_GS_RB =
+ *    red-black Gauss-Seidel (b = 1/6, red = (i+j+k) even first).
  *  Runs cycles while ||r||/||f|| (||r0|| if f = 0) > rtol and fewer than
  *  max_cycles ran; *out_rel, *out_cycles (host, may be NULL) get the last
  *  relative residual and the cycles run.  Returns STENCIL_OK or

@@ -200,6 +200,7 @@ def solve_f64(u: np.ndarray, f: np.ndarray | None, h: float, smoother: int, rtol
 
 MG_JACOBI = 0  # weighted Jacobi, omega = 6/7 (a = b = 1/7)
 MG_GS = 1      # lexicographic Gauss-Seidel
+MG_GS_RB = 2   # red-black Gauss-Seidel
 
 
 def residual32(u: np.ndarray, f: np.ndarray | None, h: float) -> np.ndarray:

@@ -371,7 +371,8 @@ int oracle_solve_f64(double* u, const double* f, int64_t nx, int64_t ny, int64_t
  * interior.
  *
  * Smoothers: 0 = weighted Jacobi with omega = 6/7 (a = 1 - omega = 1/7,
- * b = omega/6 = 1/7), 1 = lexicographic Gauss-Seidel (b = 1/6).
+ * b = omega/6 = 1/7), 1 = lexicographic Gauss-Seidel (b = 1/6), 2 = red-black
+ * Gauss-Seidel (b = 1/6; red = (i+j+k) even first).
  *
  * Restriction (full weighting, weights 1/4, 1/2, 1/4 per axis), in this order:
  *   along x:  sx = (0.25*r[i-1] + 0.5*r[i]) + 0.25*r[i+1]
@@ -401,8 +402,10 @@ static void orc_mg_smooth(orc_level* L, int smoother, int nsweeps) {
   if (nsweeps <= 0) return;
   if (smoother == 0)
     oracle_jacobi_f64(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, 1.0 / 7.0, 1.0 / 7.0, nsweeps);
-  else
+  else if (smoother == 1)
     oracle_gs_lex_f64(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, 1.0 / 6.0, nsweeps);
+  else
+    oracle_gs_rb_f64(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, 1.0 / 6.0, nsweeps);
 }
 
 /* fc (coarse interior) = full weighting of r (fine interior). */
@@ -480,7 +483,7 @@ int oracle_mg_solve_f64(double* u, const double* f, int64_t nx, int64_t ny, int6
                         int nu1, int nu2, int ncoarse, int max_levels, double rtol, int max_cycles, double* out_rel,
                         int* out_cycles) {
   orc_grid g0;
-  if (!u || orc_grid_make(&g0, nx, ny, nz) != ORC_OK || !(h > 0.0) || (smoother != 0 && smoother != 1) ||
+  if (!u || orc_grid_make(&g0, nx, ny, nz) != ORC_OK || !(h > 0.0) || (smoother < 0 || smoother > 2) ||
       nu1 < 0 || nu2 < 0 || ncoarse < 0 || max_levels < 1 || max_levels > 32 || max_cycles < 0)
     return ORC_ERR_ARG;
   orc_level lv[32];
@@ -639,8 +642,10 @@ static void orc_mg_smooth32(orc_level32* L, int smoother, int nsweeps) {
   if (nsweeps <= 0) return;
   if (smoother == 0)
     oracle_jacobi_f32(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, (float)(1.0 / 7.0), (float)(1.0 / 7.0), nsweeps);
-  else
+  else if (smoother == 1)
     oracle_gs_lex_f32(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, (float)(1.0 / 6.0), nsweeps);
+  else
+    oracle_gs_rb_f32(L->u, L->f, L->g.nx, L->g.ny, L->g.nz, L->h, (float)(1.0 / 6.0), nsweeps);
 }
 
 static void orc_vcycle32(orc_level32* lv, int l, int nlev, int smoother, int nu1, int nu2, int ncoarse) {
@@ -664,7 +669,7 @@ static void orc_vcycle32(orc_level32* lv, int l, int nlev, int smoother, int nu1
 int oracle_mg_cycles_f32(float* u, const float* f, int64_t nx, int64_t ny, int64_t nz, double h, int smoother,
                          int nu1, int nu2, int ncoarse, int max_levels, int ncycles) {
   orc_grid g0;
-  if (!u || !f || orc_grid_make(&g0, nx, ny, nz) != ORC_OK || !(h > 0.0) || (smoother != 0 && smoother != 1) ||
+  if (!u || !f || orc_grid_make(&g0, nx, ny, nz) != ORC_OK || !(h > 0.0) || (smoother < 0 || smoother > 2) ||
       nu1 < 0 || nu2 < 0 || ncoarse < 0 || max_levels < 1 || max_levels > 32 || ncycles < 0)
     return ORC_ERR_ARG;
   orc_level32 lv[32];
@@ -708,7 +713,7 @@ int oracle_solve_mixed_mg(double* u, const double* f, int64_t nx, int64_t ny, in
                           double* out_rel, int* out_iters) {
   orc_grid g;
   if (!u || orc_grid_make(&g, nx, ny, nz) != ORC_OK || !(h > 0.0) || max_outer < 0 || inner_cycles < 0 ||
-      (smoother != 0 && smoother != 1))
+      (smoother < 0 || smoother > 2))
     return ORC_ERR_ARG;
   size_t n = orc_total(&g);
   double* r = (double*)calloc(n, sizeof(double));

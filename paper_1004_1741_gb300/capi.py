@@ -29,6 +29,7 @@ STENCIL_ERR_CANCELLED = -7
 
 STENCIL_JACOBI = 0
 STENCIL_GS = 1
+STENCIL_GS_RB = 2  # multigrid smoother only
 STENCIL_F64 = 0
 STENCIL_F32 = 1
 

@@ -30,8 +30,8 @@ __global__ void __launch_bounds__(32 * RB_BY) gs_rb_kernel(T* u, const T* __rest
 }
 
 template <typename T>
-static int gs_rb_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
-                     const stencil_params* p, cudaStream_t st) {
+int gs_rb_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps, const stencil_params* p,
+              cudaStream_t st) {
   if (nsweeps == 0 || g.nx == 0 || g.ny == 0 || g.nz == 0) return STENCIL_OK;
   Coef<T> c;
   c.a = T(0);
@@ -52,6 +52,11 @@ static int gs_rb_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h
   if (e != cudaSuccess) return cuda_err(ctx, e, "gs_rb_kernel launch");
   return STENCIL_OK;
 }
+
+template int gs_rb_run<double>(stencil_ctx*, double*, const double*, const Geom&, double, int, const stencil_params*,
+                               cudaStream_t);
+template int gs_rb_run<float>(stencil_ctx*, float*, const float*, const Geom&, double, int, const stencil_params*,
+                              cudaStream_t);
 
 static int rb_checks(stencil_ctx* ctx, const void* u, const int64_t dims[3], double h, int nsweeps,
                      const stencil_params* p, Geom* g) {

@@ -101,6 +101,10 @@ int jacobi_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int 
 template <typename T>
 int gs_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps,
            const stencil_params* p, cudaStream_t st);
+// red-black Gauss-Seidel sweeps (gs_rb.cu; params: b only)
+template <typename T>
+int gs_rb_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int nsweeps, const stencil_params* p,
+              cudaStream_t st);
 // g[i] = hh * f[i] over n elements, with the site update's multiplication (ArithPreF sweeps then add g as
 // it is and give the same bits); one grid-stride launch on st.
 cudaError_t prescale_f(const double* f, double* g, size_t n, double hh, int sm_count, cudaStream_t st);

@@ -7,8 +7,8 @@
 // 2I+1); nu1 smoothing sweeps, residual, full-weighting restriction, the
 // coarse correction from zero with zero Dirichlet values, trilinear
 // prolongation added to u, nu2 smoothing sweeps; ncoarse sweeps on the
-// coarsest level.  Smoothers: weighted Jacobi with omega = 6/7 (a = b = 1/7)
-// or lexicographic Gauss-Seidel (b = 1/6).  The transfers are written in one
+// coarsest level.  Smoothers: weighted Jacobi with omega = 6/7 (a = b = 1/7),
+// lexicographic Gauss-Seidel (b = 1/6) or red-black Gauss-Seidel (b = 1/6).  The transfers are written in one
 // fixed order of IEEE operations (x, then y, then z; each weighted mean as
 // ((w a + w' b) + w c), each interpolated mean as (a + b) * 0.5), so the
 // whole cycle is deterministic and the same bits as the serial definition.
@@ -106,7 +106,7 @@ struct MGRun {
 };
 
 // Smoothing sweeps on level l in the level's precision: weighted Jacobi
-// (a = b = 1/7 rounded to T) or lexicographic Gauss-Seidel (b = 1/6).
+// (a = b = 1/7 rounded to T), lexicographic or red-black Gauss-Seidel (b = 1/6).
 template <typename T>
 int mg_smooth(MGRun<T>& m, int l, int nsweeps) {
   if (nsweeps <= 0) return STENCIL_OK;
@@ -118,6 +118,7 @@ int mg_smooth(MGRun<T>& m, int l, int nsweeps) {
     q.b = 1.0 / 7.0;
     return jacobi_run<T>(m.ctx, L.u, L.f, L.g, L.h, nsweeps, &q, m.st);
   }
+  if (m.smoother == STENCIL_GS_RB) return gs_rb_run<T>(m.ctx, L.u, L.f, L.g, L.h, nsweeps, &q, m.st);
   return gs_run<T>(m.ctx, L.u, L.f, L.g, L.h, nsweeps, &q, m.st);
 }
 
@@ -196,7 +197,8 @@ int mg_checks(stencil_ctx* ctx, const void* u, const int64_t dims[3], double h, 
   if (rc) return rc;
   if (!u) return set_err(ctx, STENCIL_ERR_ARG, "u is NULL");
   if (!(h > 0.0) || !std::isfinite(h)) return set_err(ctx, STENCIL_ERR_ARG, "h must be finite and > 0");
-  if (smoother != STENCIL_JACOBI && smoother != STENCIL_GS) return set_err(ctx, STENCIL_ERR_ARG, "bad smoother");
+  if (smoother != STENCIL_JACOBI && smoother != STENCIL_GS && smoother != STENCIL_GS_RB)
+    return set_err(ctx, STENCIL_ERR_ARG, "bad smoother");
   if (nu1 < 0 || nu2 < 0 || ncoarse < 0 || max_cycles < 0 || !(rtol >= 0.0))
     return set_err(ctx, STENCIL_ERR_ARG, "bad sweep counts or limits");
   if (max_levels < 1 || max_levels > 32) return set_err(ctx, STENCIL_ERR_ARG, "max_levels must be in 1..32");

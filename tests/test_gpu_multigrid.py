@@ -17,7 +17,8 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU-only hosts skip at c
 from paper_1004_1741_gb300 import capi  # noqa: E402
 
 DEV = torch.device("cuda:0")
-SM = {"jacobi": (capi.STENCIL_JACOBI, oracle.MG_JACOBI), "gs": (capi.STENCIL_GS, oracle.MG_GS)}
+SM = {"jacobi": (capi.STENCIL_JACOBI, oracle.MG_JACOBI), "gs": (capi.STENCIL_GS, oracle.MG_GS),
+      "gs_rb": (capi.STENCIL_GS_RB, oracle.MG_GS_RB)}
 
 
 @pytest.fixture(scope="module")
@@ -50,7 +51,7 @@ def _case(ctx, u0, f0, h, smoother, nu1, nu2, ncoarse, levels, cycles):
     return u.cpu().numpy(), ref
 
 
-@pytest.mark.parametrize("smoother", ["gs", "jacobi"])
+@pytest.mark.parametrize("smoother", ["gs", "jacobi", "gs_rb"])
 @pytest.mark.parametrize("dims", [(31, 31, 31), (15, 7, 31), (9, 9, 9), (63, 15, 7), (3, 3, 3), (1, 5, 7),
                                   (12, 9, 9), (45, 37, 23)])
 def test_mg_vcycle_bit_exact(ctx, smoother, dims):
@@ -68,7 +69,7 @@ def test_mg_vcycle_bit_exact(ctx, smoother, dims):
 def test_mg_cycle_shapes(ctx, levels, nu1, nu2, ncoarse):
     """Depth limits and sweep counts, including no pre-smoothing and no coarse sweeps."""
     u0, f0 = W.random_grid(31, 15, 31, seed=levels, with_f=True)
-    for smoother in ("gs", "jacobi"):
+    for smoother in ("gs", "jacobi", "gs_rb"):
         got, ref = _case(ctx, u0, f0, 1.0 / 32, smoother, nu1, nu2, ncoarse, levels, 2)
         _assert_exact(got, ref, "mg shape %s %s" % (smoother, (levels, nu1, nu2, ncoarse)))
 
@@ -131,7 +132,7 @@ def _mixed_case(ctx, u0, f0, h, smoother, nu1, nu2, ncoarse, levels, outer, inne
     return u.cpu().numpy(), ref
 
 
-@pytest.mark.parametrize("smoother", ["gs", "jacobi"])
+@pytest.mark.parametrize("smoother", ["gs", "jacobi", "gs_rb"])
 @pytest.mark.parametrize("dims", [(31, 31, 31), (15, 7, 31), (63, 15, 7), (3, 3, 3), (1, 5, 7), (12, 9, 9),
                                   (45, 37, 23)])
 def test_mixed_mg_bit_exact(ctx, smoother, dims):
@@ -149,12 +150,12 @@ def test_mixed_mg_bit_exact(ctx, smoother, dims):
 @pytest.mark.parametrize("levels,nu1,nu2,ncoarse", [(1, 2, 2, 3), (3, 0, 2, 1), (32, 3, 1, 0)])
 def test_mixed_mg_cycle_shapes(ctx, levels, nu1, nu2, ncoarse):
     u0, f0 = W.random_grid(31, 15, 31, seed=10 + levels, with_f=True)
-    for smoother in ("gs", "jacobi"):
+    for smoother in ("gs", "jacobi", "gs_rb"):
         got, ref = _mixed_case(ctx, u0, f0, 1.0 / 32, smoother, nu1, nu2, ncoarse, levels, 2, 1)
         _assert_exact(got, ref, "mixed mg shape %s %s" % (smoother, (levels, nu1, nu2, ncoarse)))
 
 
-@pytest.mark.parametrize("smoother", ["gs", "jacobi"])
+@pytest.mark.parametrize("smoother", ["gs", "jacobi", "gs_rb"])
 def test_mixed_mg_reaches_1e10_like_fp64_mg(ctx, smoother):
     """The sine-mode problem (8 modes + noise) at 63^3: the mixed solve reaches ||r||/||f|| <= 1e-10
     in as many outer iterations (+-1) as the FP64 multigrid needs cycles, and the two solutions agree

@@ -522,7 +522,7 @@ def test_mg_prolongation_of_a_spike_is_the_hat_function():
         np.testing.assert_array_equal(u, want)
 
 
-@pytest.mark.parametrize("smoother,bound", [(oracle.MG_GS, 0.2), (oracle.MG_JACOBI, 0.32)])
+@pytest.mark.parametrize("smoother,bound", [(oracle.MG_GS, 0.2), (oracle.MG_JACOBI, 0.32), (oracle.MG_GS_RB, 0.2)])
 def test_mg_vcycle_reduces_the_error_by_a_fixed_factor(smoother, bound):
     """Laplace problem with zero Dirichlet data (solution 0) from a random start:
     every V(2,2) cycle shrinks the error by a grid-independent factor (textbook
@@ -541,7 +541,7 @@ def test_mg_vcycle_reduces_the_error_by_a_fixed_factor(smoother, bound):
             prev = cur
 
 
-@pytest.mark.parametrize("smoother", [oracle.MG_GS, oracle.MG_JACOBI])
+@pytest.mark.parametrize("smoother", [oracle.MG_GS, oracle.MG_JACOBI, oracle.MG_GS_RB])
 def test_mg_solve_reaches_closed_form(smoother):
     """f a sum of sine modes: the V-cycles converge to u* = sum a phi / lambda
     (the discrete solution, to rounding) within a handful of cycles."""
@@ -549,7 +549,7 @@ def test_mg_solve_reaches_closed_form(smoother):
     h, f, ustar = _sine_rhs(n, [(1, 1, 1), (2, 1, 3), (5, 7, 2)], [1.0, -0.7, 0.4])
     u, rel, cycles, ok = oracle.mg_solve(np.zeros_like(f), f, h, smoother, 2, 2, 20, 8, 1e-11, 40)
     assert ok and rel <= 1e-11
-    assert cycles <= (15 if smoother == oracle.MG_GS else 25)
+    assert cycles <= (25 if smoother == oracle.MG_JACOBI else 15)
     assert np.abs(u - ustar).max() <= 1e-9 * np.abs(ustar).max()
 
 
@@ -568,6 +568,8 @@ def test_mg_one_level_is_plain_smoothing():
         np.testing.assert_array_equal(got, oracle.gs_lex(u0, f, h, 5))
         got, _, _, _ = oracle.mg_solve(u0, f, h, oracle.MG_JACOBI, 3, 3, 5, levels, 0.0, 1)
         np.testing.assert_array_equal(got, oracle.jacobi(u0, f, h, 5, a=1.0 / 7.0, b=1.0 / 7.0))
+        got, _, _, _ = oracle.mg_solve(u0, f, h, oracle.MG_GS_RB, 3, 3, 5, levels, 0.0, 1)
+        np.testing.assert_array_equal(got, oracle.gs_rb(u0, f, h, 5))
 
 
 # ------------------------------------------------- FP32 sparse forms ----
@@ -696,7 +698,7 @@ def test_mg_f32_transfers_are_exact_on_linear_functions(dims):
     np.testing.assert_array_equal(u, want.astype(np.float32))
 
 
-@pytest.mark.parametrize("smoother,bound", [(oracle.MG_GS, 0.2), (oracle.MG_JACOBI, 0.32)])
+@pytest.mark.parametrize("smoother,bound", [(oracle.MG_GS, 0.2), (oracle.MG_JACOBI, 0.32), (oracle.MG_GS_RB, 0.2)])
 def test_mg_f32_vcycle_reduces_the_error_by_a_fixed_factor(smoother, bound):
     """The FP32 V(2,2) cycle on the zero-data Laplace problem shrinks a random error by the
     textbook grid-independent factor while the error is far above the binary32 floor."""
@@ -726,9 +728,11 @@ def test_mg_f32_one_level_is_plain_fp32_smoothing():
         got = oracle.mg_cycles32(u0, f, h, oracle.MG_JACOBI, 3, 3, 5, levels, 1)
         np.testing.assert_array_equal(got, oracle.jacobi(u0, f, h, 5, a=float(np.float32(1 / 7)),
                                                          b=float(np.float32(1 / 7))))
+        got = oracle.mg_cycles32(u0, f, h, oracle.MG_GS_RB, 3, 3, 5, levels, 1)
+        np.testing.assert_array_equal(got, oracle.gs_rb(u0, f, h, 5))
 
 
-@pytest.mark.parametrize("smoother", [oracle.MG_GS, oracle.MG_JACOBI])
+@pytest.mark.parametrize("smoother", [oracle.MG_GS, oracle.MG_JACOBI, oracle.MG_GS_RB])
 def test_solve_mixed_mg_reaches_closed_form(smoother):
     """Defect correction with FP32 V-cycles inside: the FP64 residual reaches 1e-11 and u the
     closed-form discrete solution u* = sum a phi / lambda, in about as many outer iterations as
