@@ -866,7 +866,7 @@ def run_suite_served(args):
             h = 1.0 / (nn + 1)
             if r.kind == "solve":
                 cyc = 0
-                rel, cyc, _ = capi.stencil_mg_solve(ctx, u, f, h, capi.STENCIL_GS, nu1=2, nu2=2, ncoarse=args.quantum,
+                rel, cyc, _ = capi.stencil_mg_solve(ctx, u, f, h, capi.STENCIL_GS_RB, nu1=2, nu2=2, ncoarse=args.quantum,
                                                     rtol=r.rtol, max_cycles=r.sweeps // 4)
                 lup += 4.0 * cyc * nn ** 3
             else:

@@ -321,10 +321,10 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
 #define STENCIL_REQ_JACOBI 0 /* nsweeps Jacobi sweeps */
 #define STENCIL_REQ_GS 1     /* nsweeps Gauss-Seidel sweeps */
 #define STENCIL_REQ_SOLVE 2  /* solve until ||f-Au||/||f|| <= rtol (FP64 only): multigrid V(2,2) cycles with the
-                              * Gauss-Seidel smoother (stencil_mg_solve, sweeps_per_round sweeps on the coarsest
-                              * level) when every extent is odd and >= 3, else Gauss-Seidel sweeps; nsweeps caps
-                              * the fine-grid sweeps, a cycle counting 4; the residual is tested after each cycle
-                              * or round of sweeps */
+                              * red-black Gauss-Seidel smoother (stencil_mg_solve, sweeps_per_round sweeps on the
+                              * coarsest level) when every extent is odd and >= 3, else lexicographic Gauss-Seidel
+                              * sweeps; nsweeps caps the fine-grid sweeps, a cycle counting 4; the residual is
+                              * tested after each cycle or round of sweeps */
 
 typedef struct stencil_server stencil_server;
 

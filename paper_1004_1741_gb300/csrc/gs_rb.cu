@@ -4,6 +4,7 @@
 // of one colour read only the other colour, so each colour is one fully
 // parallel launch and any order within it gives the same bits.
 #include <cmath>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -20,12 +21,15 @@ __global__ void __launch_bounds__(32 * RB_BY) gs_rb_kernel(T* u, const T* __rest
   const int z0 = blockIdx.z * RB_ZCHUNK, z1 = min(g.nz, z0 + RB_ZCHUNK);
   const int64_t sx = g.sx, sy = g.sy;
   for (int z = z0; z < z1; ++z) {
+    // a warp is one row: every lane takes part in the adaptive arithmetic's vote; lanes past the row's
+    // last site of this colour read the last site's neighbours and store nothing
     const int x = 2 * xi + ((y + z + colour) & 1);
-    if (x >= g.nx) continue;
-    T* q = u + g.at(x, y, z);
+    const bool act = x < g.nx;
+    T* q = u + g.at(act ? x : g.nx - 1, y, z);
     T fv = T(0);
     if (HAS_F) fv = f[q - u];
-    *q = site_update<T, Ar, HAS_F, false>(q[-1], q[1], q[-sx], q[sx], q[-sy], q[sy], fv, T(0), c);
+    const T v = site_update_warp<T, Ar, HAS_F, false>(act, q[-1], q[1], q[-sx], q[sx], q[-sy], q[sy], fv, T(0), c);
+    if (act) *q = v;
   }
 }
 
@@ -37,7 +41,9 @@ int gs_rb_run(stencil_ctx* ctx, T* u, const T* f, const Geom& g, double h, int n
   c.a = T(0);
   c.b = (T)((p && p->b != 0.0) ? p->b : 1.0 / 6.0);
   c.hh = (T)(h * h);
-  using Ar = typename DefaultArith<T>::type;
+  // FP64: the adaptive arithmetic (per warp: three integer-pipe additions for non-negative neighbourhoods,
+  // else the multiplication in integer arithmetic; the same bits)
+  using Ar = typename std::conditional<sizeof(T) == 8, AdaptJacobi, typename DefaultArith<T>::type>::type;
   dim3 block(32, RB_BY);
   dim3 grid((g.nx / 2 + 1 + 31) / 32, (g.ny + RB_BY - 1) / RB_BY, (g.nz + RB_ZCHUNK - 1) / RB_ZCHUNK);
   for (int s = 0; s < nsweeps; ++s)

@@ -8,7 +8,8 @@
 // the compute thread runs rounds over the requests on the device: up to
 // `sweeps_per_round` sweeps of every smoothing request, all requests of one
 // (smoother, dtype) class in ONE persistent batched launch
-// (stencil_batched), and one multigrid V-cycle of every solve request.
+// (stencil_batched), and one multigrid V-cycle (red-black Gauss-Seidel
+// smoother) of every solve request.
 // Copies of requests arriving or leaving overlap the rounds' kernels.
 // A request's result does not depend on the other requests in the mix: the
 // batched kernel is exact per grid, sweeps split into rounds compose exactly,
@@ -188,8 +189,8 @@ static bool copy_step(stencil_server* s) {
 //
 // Smoothing requests: up to `quantum` sweeps each, all requests of one
 // (smoother, dtype) class in one batched launch.  Solve requests: one
-// multigrid V(2,2) cycle each (lexicographic Gauss-Seidel smoother; plain
-// sweeps when an extent cannot coarsen), residual tested after it.  Requests
+// multigrid V(2,2) cycle each (red-black Gauss-Seidel smoother; plain
+// lexicographic sweeps when an extent cannot coarsen), residual tested after it.  Requests
 // that finish are handed to the copy thread.
 static bool compute_round(stencil_server* s) {
   std::vector<Req*> act;
@@ -253,8 +254,9 @@ static bool compute_round(stencil_server* s) {
     int cyc = 0;
     int rc = STENCIL_OK;
     if (per > 0)
-      rc = stencil_mg_solve(ctx, (double*)q->du, (const double*)q->df, q->r.dims, q->r.h, STENCIL_GS, 2, 2,
-                            levels > 1 ? s->quantum : per, levels, q->r.rtol, 1, &rel, &cyc, st);
+      rc = stencil_mg_solve(ctx, (double*)q->du, (const double*)q->df, q->r.dims, q->r.h,
+                            levels > 1 ? STENCIL_GS_RB : STENCIL_GS, 2, 2, levels > 1 ? s->quantum : per, levels,
+                            q->r.rtol, 1, &rel, &cyc, st);
     std::lock_guard<std::mutex> lk(s->mu);
     if (rc != STENCIL_OK && rc != STENCIL_ERR_NOT_CONVERGED) {
       finish(s, q, rc, -1.0);

@@ -105,7 +105,8 @@ def test_slot_limit_keeps_results_exact():
 
 
 def test_solve_request_runs_multigrid_cycles():
-    """A solve request on odd extents runs multigrid V(2,2) cycles (one per round, residual after each):
+    """A solve request on odd extents runs multigrid V(2,2) cycles with the red-black smoother (one per round,
+    residual after each):
     the result equals the oracle's multigrid solve with the same stopping test, bit for bit, four sweeps
     counted per cycle; the same request capped before convergence reports its residual."""
     p = W.sine_modes_problem(31, seed=4)
@@ -116,13 +117,13 @@ def test_solve_request_runs_multigrid_cycles():
         assert res["status"] == capi.STENCIL_OK and res["rel_residual"] <= 1e-8
         cycles = res["sweeps_done"] // 4
         assert res["sweeps_done"] == 4 * cycles and 3 <= cycles <= 15
-        ref, rel, rc, ok = oracle.mg_solve(u0, p.f, p.h, oracle.MG_GS, 2, 2, 10, 32, 1e-8, cycles)
+        ref, rel, rc, ok = oracle.mg_solve(u0, p.f, p.h, oracle.MG_GS_RB, 2, 2, 10, 32, 1e-8, cycles)
         assert ok and rc == cycles
         assert np.array_equal(out, ref)
         out2 = np.empty_like(u0)
         res2 = srv.wait(srv.submit(capi.STENCIL_REQ_SOLVE, u0, p.f, p.h, 9, rtol=1e-8, u_out=out2), 60)
         assert res2["status"] == capi.STENCIL_ERR_NOT_CONVERGED and res2["sweeps_done"] == 8
-        ref2, _, _, _ = oracle.mg_solve(u0, p.f, p.h, oracle.MG_GS, 2, 2, 10, 32, 1e-8, 2)
+        ref2, _, _, _ = oracle.mg_solve(u0, p.f, p.h, oracle.MG_GS_RB, 2, 2, 10, 32, 1e-8, 2)
         assert np.array_equal(out2, ref2)
 
 
