@@ -300,6 +300,17 @@ int stencil_set_wait_limit(stencil_ctx* ctx, long long timeout_ns, long long nev
 int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, const void* f, const int64_t dims[3],
                      double h, int nsweeps, stencil_params* out, double* out_glups, void* stream);
 
+/* Autotuner for a batch (not in the paper): times the batched paths' candidate
+ * kernel forms, temporal depths nt, tiles and (FP64) integer-pipe forms on
+ * copies of the caller's n grids (device u[i], dtype STENCIL_F64/F32; f[i] may
+ * be NULL) with their sweep counts, exactly as stencil_batched would run them,
+ * and writes the fastest into *out (its whole-batch GLUP/s into *out_glups if
+ * not NULL).  The grids are not modified.  Workspace: one copy of the batch.
+ * Blocking. */
+int stencil_autotune_batched(stencil_ctx* ctx, int n, const void* const* u, const void* const* f, const int64_t* dims,
+                             const double* h, const int* nsweeps, int smoother, int dtype, stencil_params* out,
+                             double* out_glups, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Continuous-batching server (not in the paper).
  *

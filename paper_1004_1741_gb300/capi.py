@@ -123,6 +123,8 @@ _SIGS = {
                                _P]),
     "stencil_mg_solve": (_I, [_P, _P, _P, _I64P, _D, _I, _I, _I, _I, _I, _D, _I, ctypes.POINTER(_D),
                               ctypes.POINTER(_I), _P]),
+    "stencil_autotune_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _I64P, ctypes.POINTER(_D),
+                                      ctypes.POINTER(_I), _I, _I, _PP, ctypes.POINTER(_D), _P]),
     "stencil_probe_throughput": (_I, [_P, ctypes.c_size_t, ctypes.POINTER(stencil_probe_result)]),
     "stencil_solve_mixed_mg": (_I, [_P, _P, _P, _I64P, _D, _I, _I, _I, _I, _I, _D, _I, _I, ctypes.POINTER(_D),
                                     ctypes.POINTER(_I), _P]),
@@ -347,6 +349,32 @@ def stencil_autotune(ctx: Context, smoother: int, u: torch.Tensor, f: torch.Tens
     dtype = STENCIL_F64 if u.dtype == torch.float64 else STENCIL_F32
     rc = lib.stencil_autotune(ctx.handle, int(smoother), dtype, _grid(u, u.dtype), _opt_grid(f, u, u.dtype), _dims(u),
                               float(h), int(nsweeps), ctypes.byref(out), ctypes.byref(g), _stream(stream))
+    _check(ctx, rc)
+    return ({"nt": out.nt, "tile": (out.tile_x, out.tile_y, out.tile_z), "variant": out.variant,
+             "int_adds": out.int_adds}, g.value)
+
+
+def stencil_autotune_batched(ctx: Context, us, fs, hs, nsweeps, smoother: int, stream=None):
+    """The fastest batched parameters for these grids (tensors of one dtype) and sweep counts; returns
+    (params dict for stencil_batched, whole-batch GLUP/s).  The grids are not modified."""
+    lib = load_library()
+    n = len(us)
+    dt = us[0].dtype
+    dtype = STENCIL_F64 if dt == torch.float64 else STENCIL_F32
+    up = (ctypes.c_void_p * n)(*[_grid(u, dt).value for u in us])
+    fp = None
+    if fs is not None:
+        fp = (ctypes.c_void_p * n)(*[(_opt_grid(f, u, dt).value if f is not None else None) for f, u in zip(fs, us)])
+    dims = (ctypes.c_int64 * (3 * n))()
+    for i, u in enumerate(us):
+        d = _dims(u)
+        dims[3 * i], dims[3 * i + 1], dims[3 * i + 2] = d[0], d[1], d[2]
+    hh = (ctypes.c_double * n)(*[float(x) for x in hs])
+    ns = (ctypes.c_int * n)(*[int(x) for x in nsweeps])
+    out = stencil_params()
+    g = ctypes.c_double(0.0)
+    rc = lib.stencil_autotune_batched(ctx.handle, n, up, fp, dims, hh, ns, int(smoother), dtype, ctypes.byref(out),
+                                      ctypes.byref(g), _stream(stream))
     _check(ctx, rc)
     return ({"nt": out.nt, "tile": (out.tile_x, out.tile_y, out.tile_z), "variant": out.variant,
              "int_adds": out.int_adds}, g.value)

@@ -127,6 +127,119 @@ using namespace stn;
 
 extern "C" {
 
+int stencil_autotune_batched(stencil_ctx* ctx, int n, const void* const* u, const void* const* f, const int64_t* dims,
+                             const double* h, const int* nsweeps, int smoother, int dtype, stencil_params* out,
+                             double* out_glups, void* stream) {
+  if (!ctx || !out) return STENCIL_ERR_ARG;
+  ctx->err.clear();
+  if (n <= 0 || !u || !dims || !h || !nsweeps) return set_err(ctx, STENCIL_ERR_ARG, "bad batch arrays");
+  if (smoother != STENCIL_JACOBI && smoother != STENCIL_GS) return set_err(ctx, STENCIL_ERR_ARG, "bad smoother");
+  if (dtype != STENCIL_F64 && dtype != STENCIL_F32) return set_err(ctx, STENCIL_ERR_ARG, "bad dtype %d", dtype);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t esz = dtype == STENCIL_F64 ? 8 : 4;
+  std::vector<size_t> off((size_t)n + 1, 0);
+  double lup = 0.0;
+  for (int i = 0; i < n; ++i) {
+    Geom g;
+    int rc = check_dims(ctx, dims + 3 * (size_t)i, &g);
+    if (rc) return rc;
+    off[(size_t)i + 1] = off[(size_t)i] + (size_t)g.sy * (size_t)(g.nz + 2) * esz;
+    lup += (double)g.nx * g.ny * g.nz * (nsweeps[i] > 0 ? nsweeps[i] : 0);
+  }
+  int status;
+  unsigned char* scratch = (unsigned char*)ws_get(ctx, SLOT_TUNE_GRID, off[(size_t)n], &status);
+  if (!scratch) return status;
+  std::vector<void*> copies((size_t)n);
+  for (int i = 0; i < n; ++i) copies[(size_t)i] = scratch + off[(size_t)i];
+  auto reload = [&]() -> cudaError_t {
+    for (int i = 0; i < n; ++i) {
+      cudaError_t e2 = cudaMemcpyAsync(copies[(size_t)i], u[i], off[(size_t)i + 1] - off[(size_t)i],
+                                       cudaMemcpyDeviceToDevice, st);
+      if (e2 != cudaSuccess) return e2;
+    }
+    return cudaSuccess;
+  };
+  // candidates: (variant, nt, tile, int_adds) of the batched paths
+  struct Cand {
+    int variant, nt, tx, ty, tz, int_adds;
+  };
+  const bool f64 = dtype == STENCIL_F64;
+  std::vector<Cand> cands;
+  if (smoother == STENCIL_GS) {
+    for (int ia : {-1, 2}) {
+      if (ia >= 0 && !f64) continue;
+      for (int tz : {0, 50}) {
+        cands.push_back({0, 1, 0, 0, tz, ia});  // column march, per-dtype default tile
+        cands.push_back({0, 1, 8, 8, tz, ia});
+        cands.push_back({0, 1, 16, 8, tz, ia});
+        cands.push_back({0, 1, 8, 16, tz, ia});
+      }
+      for (int nt : {2, 4}) {  // column march, nt sweeps per task
+        cands.push_back({4, nt, 8, 8, 0, ia});
+        cands.push_back({4, nt, 16, 8, 0, ia});
+      }
+    }
+    for (int nt : {1, 2, 4}) cands.push_back({3, nt, 16, 16, 16, -1});  // tile tasks
+  } else {
+    for (int ia : {-1, 3}) {
+      if (ia >= 0 && !f64) continue;
+      for (int by : {4, 8, 16}) cands.push_back({0, 1, 32, by, 0, ia});  // z-march launches per sweep
+    }
+    for (int nt : {2, 4})
+      for (int tz : {8, 16}) cands.push_back({3, nt, 32, tz == 8 ? 8 : 16, tz, -1});  // tile tasks
+  }
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_err(ctx, e, "cudaEventCreate");
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_err(ctx, e, "cudaEventCreate");
+  }
+  double best = -1.0;
+  Cand bestc = cands[0];
+  for (const Cand& c : cands) {
+    stencil_params q{};
+    q.nt = c.nt;
+    q.tile_x = c.tx;
+    q.tile_y = c.ty;
+    q.tile_z = c.tz;
+    q.variant = c.variant;
+    q.int_adds = c.int_adds;
+    auto run = [&]() -> int {
+      return f64 ? batched_run<double>(ctx, n, copies.data(), f, dims, h, nsweeps, smoother, &q, st)
+                 : batched_run<float>(ctx, n, copies.data(), f, dims, h, nsweeps, smoother, &q, st);
+    };
+    if (reload() != cudaSuccess || run() != STENCIL_OK) continue;  // warm-up (plans, tables); skip what fails
+    if (reload() != cudaSuccess) continue;
+    cudaEventRecord(e0, st);
+    const int r2 = run();
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || r2 != STENCIL_OK) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double glups = lup / (ms * 1e-3) / 1e9;
+    if (glups > best) {
+      best = glups;
+      bestc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  if (best < 0) return set_err(ctx, STENCIL_ERR_CUDA, "no candidate ran");
+  ctx->err.clear();
+  *out = stencil_params{};
+  out->nt = bestc.nt;
+  out->tile_x = bestc.tx;
+  out->tile_y = bestc.ty;
+  out->tile_z = bestc.tz;
+  out->variant = bestc.variant;
+  out->int_adds = bestc.int_adds;
+  if (out_glups) *out_glups = best;
+  return STENCIL_OK;
+}
+
 int stencil_batched(stencil_ctx* ctx, int n, void* const* u, const void* const* f, const int64_t* dims,
                     const double* h, const int* nsweeps, int smoother, int dtype, const stencil_params* params,
                     void* stream) {

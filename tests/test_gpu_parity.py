@@ -662,3 +662,24 @@ def test_batched_full_config_sampled(ctx, smoother, sweeps):
     for i in order[::16]:
         c = cases[i]
         _assert_exact(us[i].cpu().numpy(), ofn(c.u, c.f, c.h, sweeps), "batched grid %d %s" % (i, (c.nx, c.ny, c.nz)))
+
+
+@pytest.mark.parametrize("smoother", [capi.STENCIL_JACOBI, capi.STENCIL_GS])
+def test_autotune_batched_picks_a_valid_config(ctx, smoother):
+    """The whole-batch autotuner leaves the grids as they were and returns parameters that the batched call
+    runs to the oracle's bits."""
+    dims = [(40, 24, 17), (17, 33, 9), (64, 16, 20)]
+    grids = [W.random_grid(*d, seed=40 + i, with_f=True) for i, d in enumerate(dims)]
+    us = [_dev(u) for u, _ in grids]
+    fs = [_dev(f) for _, f in grids]
+    hs = [W.grid_h(*d) for d in dims]
+    sweeps = [6, 3, 5]
+    params, glups = capi.stencil_autotune_batched(ctx, us, fs, hs, sweeps, smoother)
+    assert glups > 0
+    for u, (u0, _) in zip(us, grids):
+        assert np.array_equal(u.cpu().numpy(), u0)
+    capi.stencil_batched(ctx, us, fs, hs, sweeps, smoother, **params)
+    torch.cuda.synchronize()
+    ofn = oracle.jacobi if smoother == capi.STENCIL_JACOBI else oracle.gs_lex
+    for i, (u0, f0) in enumerate(grids):
+        _assert_exact(us[i].cpu().numpy(), ofn(u0, f0, hs[i], sweeps[i]), "autotuned batch %s grid %d" % (params, i))
