@@ -538,7 +538,8 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
         with torch.cuda.stream(sg):
             og.copy_(dg, non_blocking=True)
 
-    step()
+    for _ in range(2):  # warm-up: workspace, plans, graphs of both contexts
+        step()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = max(1, min(args.steps, 3))
