@@ -606,6 +606,23 @@ def test_full_size_400_bench_config(ctx, smoother):
     _assert_exact(got, ref, "400^3 %s" % smoother)
 
 
+@pytest.mark.parametrize("name,nt", [("gs", 2), ("gs", 4), ("gs_f32", 2), ("gs_f32", 4), ("gs", 16)])
+def test_full_size_400_nt_sweep_config(ctx, name, nt):
+    """The benchmark grid in the launch configuration of the benchmark's temporal-depth sweep (the
+    multi-sweep column march at nt = 2, 4, the L1 tile tasks at nt = 16), 2 nt + 1 sweeps (the last pass
+    shorter): full field bit-exact."""
+    import bench
+
+    cfg = bench._nt_cfg(name, nt)
+    u0 = W.laplace_cube(400, dtype=np.float32 if name.endswith("f32") else np.float64)
+    ns = 2 * nt + 1
+    with cf.ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(oracle.gs_lex, u0, None, 1.0, ns)
+        got = _run(ctx, capi.stencil_gs_lex, u0, None, 1.0, ns, nt=nt, **cfg)
+        ref = fut.result()
+    _assert_exact(got, ref, "400^3 %s nt=%d" % (name, nt))
+
+
 # ------------------------------------------------------------ in-place Jacobi --
 @pytest.mark.parametrize("dims", RAGGED + [(45, 38, 29), (33, 9, 70)])
 @pytest.mark.parametrize("slab", [0, 1, 2, 7, 32, 1000])
