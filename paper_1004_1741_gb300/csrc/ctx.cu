@@ -71,6 +71,7 @@ void* ws_get(stencil_ctx* ctx, SlotId id, size_t bytes, int* status) {
   }
   s.ptr = p;
   s.bytes = grown;
+  ctx->ws_gen++;
   ctx->held += grown;
   return p;
 }
@@ -148,6 +149,9 @@ void stencil_destroy(stencil_ctx* ctx) {
     if (s.ptr) cudaFree(s.ptr);
   for (auto& en : ctx->slices)
     if (en.dev) cudaFree(en.dev);
+  for (auto& mg : ctx->mg_graphs)
+    if (mg.exec) cudaGraphExecDestroy(mg.exec);
+  if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
   if (ctx->ev) cudaEventDestroy(ctx->ev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   delete ctx;

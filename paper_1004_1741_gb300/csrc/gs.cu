@@ -186,6 +186,7 @@ int ensure_slices(stencil_ctx* ctx, const TileGeom& tg, cudaStream_t st) {
     cudaFree(ctx->slices[lru].dev);
     ctx->held -= ctx->slices[lru].bytes;
     ctx->slices.erase(ctx->slices.begin() + (long)lru);
+    ctx->ws_gen++;
   }
   if (ctx->budget && ctx->held + bytes > ctx->budget)
     return set_err(ctx, STENCIL_ERR_OOM, "tile-slice table needs %zu bytes; %zu held, budget %zu", bytes, ctx->held,

@@ -46,6 +46,14 @@ enum SlotId {
 }  // namespace stn
 
 namespace stn {
+// A multigrid V-cycle captured as a CUDA graph, for the arguments and workspace in `key`.
+struct MGGraph {
+  std::vector<int64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long nlaunch = 0;  // kernels one replay launches
+  unsigned long long last_use = 0;
+  int uses = 0;                    // calls seen; -1: capture failed, always launch directly
+};
 // One tile-slice table (tiles (I,J,K) grouped by I+J+K) on the device, for one tile-count shape.
 struct SliceEntry {
   int NI = 0, NJ = 0, NK = 0;
@@ -69,6 +77,12 @@ struct stencil_ctx {
   std::vector<stn::SliceEntry> slices;
   int slice_cur = -1;
   unsigned long long slice_clock = 0;
+  // device buffers a captured graph may refer to change only when this counter moves (a workspace slot
+  // reallocated, a slice table evicted); multigrid cycles captured as graphs, keyed by it
+  unsigned long long ws_gen = 0;
+  std::vector<stn::MGGraph> mg_graphs;
+  unsigned long long mg_clock = 0;
+  cudaStream_t cstream = nullptr;  // stream for capturing multigrid cycles
   int64_t goff_key[6] = {0, 0, 0, 0, 0, 0};  // (W, H, D, nt, sx, sy) of SLOT_GS_GOFF
   int sm_count = 0;
   unsigned long long launches = 0;  // kernels this context has launched

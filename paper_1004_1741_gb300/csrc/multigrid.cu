@@ -15,7 +15,10 @@
 // The same cycle runs in binary32 (every operation in float, the FP32
 // residual and smoothers) as the inner solver of the mixed-precision defect
 // correction stencil_solve_mixed_mg, whose residual and update stay FP64.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -155,6 +158,79 @@ int mg_vcycle(MGRun<T>& m, int l) {
   return mg_smooth(m, l, m.nu2);
 }
 
+// One V-cycle, replayed from a CUDA graph once the same cycle recurs.  A call's
+// first cycle with given arguments runs its launches directly (it also sets up
+// the workspace and tile tables); the next one is captured into a graph (one
+// launch of some hundred kernels instead of as many launches, which is what
+// bounds the cycles of small grids); later ones replay it.  The graph is kept
+// in the context, keyed by the arguments, every level's buffers and the
+// workspace generation (a reallocated slot or an evicted table makes a new
+// key), for later calls on the same grids (the served solves call once per
+// round).  A capture that fails falls back to direct launches.
+template <typename T>
+int mg_cycle(MGRun<T>& m) {
+  stencil_ctx* ctx = m.ctx;
+  std::vector<int64_t> key = {(int64_t)sizeof(T), m.smoother, m.nu1, m.nu2, m.ncoarse, (int64_t)m.lv.size(),
+                              (int64_t)(intptr_t)m.r, (int64_t)ctx->ws_gen};
+  for (const MGLevel<T>& L : m.lv) {
+    int64_t hb;
+    memcpy(&hb, &L.h, sizeof(hb));
+    key.insert(key.end(), {L.g.nx, L.g.ny, L.g.nz, hb, (int64_t)(intptr_t)L.u, (int64_t)(intptr_t)L.f});
+  }
+  MGGraph* e = nullptr;
+  for (MGGraph& c : ctx->mg_graphs)
+    if (c.key == key) e = &c;
+  if (!e) {
+    if (ctx->mg_graphs.size() >= 32) {  // drop the least recently used
+      auto it = std::min_element(ctx->mg_graphs.begin(), ctx->mg_graphs.end(),
+                                 [](const MGGraph& a, const MGGraph& b) { return a.last_use < b.last_use; });
+      if (it->exec) cudaGraphExecDestroy(it->exec);
+      ctx->mg_graphs.erase(it);
+    }
+    ctx->mg_graphs.push_back(MGGraph{});
+    e = &ctx->mg_graphs.back();
+    e->key = key;
+  }
+  e->last_use = ++ctx->mg_clock;
+  if (e->exec) {
+    cudaError_t err = cudaGraphLaunch(e->exec, m.st);
+    if (err != cudaSuccess) return cuda_err(ctx, err, "multigrid cycle graph");
+    ctx->launches += e->nlaunch;
+    return STENCIL_OK;
+  }
+  if (e->uses < 0) return mg_vcycle(m, 0);     // a capture of these arguments failed before
+  if (e->uses++ == 0) return mg_vcycle(m, 0);  // first use: direct
+  if (!ctx->cstream) {
+    cudaError_t err = cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking);
+    if (err != cudaSuccess) return cuda_err(ctx, err, "cudaStreamCreate");
+  }
+  MGRun<T> mc = m;
+  mc.st = ctx->cstream;
+  const unsigned long long l0 = ctx->launches;
+  const std::string saved = ctx->err;
+  cudaError_t err = cudaStreamBeginCapture(mc.st, cudaStreamCaptureModeThreadLocal);
+  int rc = err == cudaSuccess ? mg_vcycle(mc, 0) : STENCIL_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  if (err == cudaSuccess) err = cudaStreamEndCapture(mc.st, &graph);
+  const unsigned long long n = ctx->launches - l0;
+  ctx->launches = l0;  // the capture launched nothing
+  cudaGraphExec_t exec = nullptr;
+  if (rc == STENCIL_OK && err == cudaSuccess && graph) err = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc != STENCIL_OK || err != cudaSuccess || !exec) {
+    cudaGetLastError();
+    ctx->err = saved;
+    e->uses = -1;
+    return mg_vcycle(m, 0);
+  }
+  e->exec = exec;
+  e->nlaunch = n;
+  err = cudaGraphLaunch(exec, m.st);
+  if (err != cudaSuccess) return cuda_err(ctx, err, "multigrid cycle graph");
+  ctx->launches += n;
+  return STENCIL_OK;
+}
+
 // Builds the level hierarchy over (u, f) on g0 and takes its workspace: every
 // coarse level's correction and right-hand side from slot `levels` (halos
 // zeroed once), one residual grid of the finest size from slot `rslot`.
@@ -237,7 +313,7 @@ extern "C" int stencil_mg_solve(stencil_ctx* ctx, double* u, const double* f, co
   double rel = denom > 0.0 ? rn / denom : 0.0;
   int it = 0;
   while (rel > rtol && it < max_cycles) {
-    if ((rc = mg_vcycle(m, 0))) return rc;
+    if ((rc = mg_cycle(m))) return rc;
     ++it;
     if ((rc = residual_launch(ctx, u, f, g0, h, nullptr, nullptr, &dres, m.st))) return rc;
     if ((rc = read_sums(ctx, dres, sums, m.st))) return rc;
@@ -291,7 +367,7 @@ extern "C" int stencil_solve_mixed_mg(stencil_ctx* ctx, double* u, const double*
     e = cudaMemsetAsync(e32, 0, n * sizeof(float), st);
     if (e != cudaSuccess) return cuda_err(ctx, e, "memset e32");
     for (int c = 0; c < inner_cycles; ++c)
-      if ((rc = mg_vcycle(m, 0))) return rc;
+      if ((rc = mg_cycle(m))) return rc;
     if ((rc = correct_launch(ctx, u, e32, g0, st))) return rc;
     ++it;
     if ((rc = residual_launch(ctx, u, f, g0, h, nullptr, r32, &dres, st))) return rc;
