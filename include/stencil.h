@@ -322,8 +322,9 @@ int stencil_autotune_batched(stencil_ctx* ctx, int n, const void* const* u, cons
  * own, where they stay until completion, and copies finished grids back.  A
  * compute thread runs rounds over the requests on the device: up to
  * sweeps_per_round sweeps (0 = 10) of every smoothing request -- all requests
- * of one (smoother, dtype) class in ONE batched persistent launch -- and one
- * multigrid cycle of every solve request.  Requests that arrive meanwhile are
+ * of one (smoother, dtype) class in ONE batched persistent launch -- and up
+ * to sweeps_per_round / 4 multigrid cycles (at least one) of every solve
+ * request.  Requests that arrive meanwhile are
  * admitted as memory and slots free up; their copies overlap the rounds'
  * kernels.  A request's result is the same alone and in any mix.
  * ------------------------------------------------------------------------- */

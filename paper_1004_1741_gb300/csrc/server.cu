@@ -188,9 +188,10 @@ static bool copy_step(stencil_server* s) {
 // --- compute thread: one round over the requests on the device --------------
 //
 // Smoothing requests: up to `quantum` sweeps each, all requests of one
-// (smoother, dtype) class in one batched launch.  Solve requests: one
-// multigrid V(2,2) cycle each (red-black Gauss-Seidel smoother; plain
-// lexicographic sweeps when an extent cannot coarsen), residual tested after it.  Requests
+// (smoother, dtype) class in one batched launch.  Solve requests: up to
+// quantum / 4 multigrid V(2,2) cycles each (red-black Gauss-Seidel smoother;
+// plain lexicographic sweeps when an extent cannot coarsen), the residual
+// tested after every cycle.  Requests
 // that finish are handed to the copy thread.
 static bool compute_round(stencil_server* s) {
   std::vector<Req*> act;
@@ -247,16 +248,18 @@ static bool compute_round(stencil_server* s) {
     const bool odd = q->r.dims[0] % 2 && q->r.dims[1] % 2 && q->r.dims[2] % 2 && q->r.dims[0] >= 3 &&
                      q->r.dims[1] >= 3 && q->r.dims[2] >= 3;
     const int rem = q->r.nsweeps - q->done_sweeps;
-    // a V(2,2) cycle counts four fine-grid sweeps; one level: min(quantum, rem) sweeps per round
+    // a V(2,2) cycle counts four fine-grid sweeps: up to quantum / 4 cycles per round (at least one), within
+    // the cap; one level: min(quantum, rem) sweeps per round
     const int levels = odd && rem >= 4 ? 32 : 1;
     const int per = levels > 1 ? 4 : std::min(s->quantum, rem);
+    const int maxc = levels > 1 ? std::max(1, std::min(s->quantum / 4, rem / 4)) : 1;
     double rel = -1.0;
     int cyc = 0;
     int rc = STENCIL_OK;
     if (per > 0)
       rc = stencil_mg_solve(ctx, (double*)q->du, (const double*)q->df, q->r.dims, q->r.h,
                             levels > 1 ? STENCIL_GS_RB : STENCIL_GS, 2, 2, levels > 1 ? s->quantum : per, levels,
-                            q->r.rtol, 1, &rel, &cyc, st);
+                            q->r.rtol, maxc, &rel, &cyc, st);
     std::lock_guard<std::mutex> lk(s->mu);
     if (rc != STENCIL_OK && rc != STENCIL_ERR_NOT_CONVERGED) {
       finish(s, q, rc, -1.0);

@@ -105,8 +105,8 @@ def test_slot_limit_keeps_results_exact():
 
 
 def test_solve_request_runs_multigrid_cycles():
-    """A solve request on odd extents runs multigrid V(2,2) cycles with the red-black smoother (one per round,
-    residual after each):
+    """A solve request on odd extents runs multigrid V(2,2) cycles with the red-black smoother (up to
+    sweeps_per_round / 4 per round, residual after each):
     the result equals the oracle's multigrid solve with the same stopping test, bit for bit, four sweeps
     counted per cycle; the same request capped before convergence reports its residual."""
     p = W.sine_modes_problem(31, seed=4)
