@@ -843,6 +843,7 @@ def run_suite_served(args):
                 "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "glups_busy": st["glups"],
                 "smoothing_glups": st["smooth_lup"] / st["smooth_s"] / 1e9 if st["smooth_s"] > 0 else None,
                 "solve_cycles": st["solve_cycles"], "solve_s": st["solve_s"], "smoothing_s": st["smooth_s"],
+                "copy_gb": st["copy_bytes"] / 1e9, "copy_s": st["copy_s"],
                 "glups_wall": st["lup_total"] / t_end / 1e9, "lup": st["lup_total"], "busy_s": st["busy_s"],
                 "wall_s": t_end, "arrival_window_s": t_arr, "hbm_peak_gb": st["hbm_peak"] / 1e9,
                 "launches": st["launches"]}
@@ -853,7 +854,7 @@ def run_suite_served(args):
         dev = torch.device("cuda", 0)
         t0 = time.perf_counter()
         lat, lup, n = [], 0.0, 0
-        t_smooth, lup_smooth = 0.0, 0.0
+        t_smooth, lup_smooth, t_copy = 0.0, 0.0, 0.0
         for r in reqs:
             if r.arrival_s > window:
                 break
@@ -862,8 +863,11 @@ def run_suite_served(args):
                 time.sleep(r.arrival_s - now)
             nn, dt = shape(r)
             uh, fh = inputs(nn, dt)
+            tc = time.perf_counter()
             u = torch.from_numpy(uh).to(dev)
             f = torch.from_numpy(fh).to(dev)
+            torch.cuda.synchronize()
+            t_copy += time.perf_counter() - tc
             h = 1.0 / (nn + 1)
             if r.kind == "solve":
                 cyc = 0
@@ -878,14 +882,18 @@ def run_suite_served(args):
                 t_smooth += time.perf_counter() - ts
                 lup += float(r.sweeps) * nn ** 3
                 lup_smooth += float(r.sweeps) * nn ** 3
+            torch.cuda.synchronize()
+            tc = time.perf_counter()
             u.cpu()
+            t_copy += time.perf_counter() - tc
             lat.append(time.perf_counter() - t0 - r.arrival_s)
             n += 1
         t_end = time.perf_counter() - t0
         ctx.close()
         lat.sort()
         return {"completed": n, "p50_s": pct(lat, 0.5), "p99_s": pct(lat, 0.99), "glups_wall": lup / t_end / 1e9,
-                "smoothing_glups": lup_smooth / t_smooth / 1e9 if t_smooth > 0 else None, "wall_s": t_end}
+                "smoothing_glups": lup_smooth / t_smooth / 1e9 if t_smooth > 0 else None, "copy_s": t_copy,
+                "wall_s": t_end}
 
     out = []
     for rate in rates:

@@ -370,6 +370,7 @@ typedef struct stencil_server_stats {
   int queue_depth, active;
   double smooth_lup, smooth_s; /* smoothing requests: updates and seconds of their batched launches */
   double solve_cycles, solve_s; /* solve requests: multigrid cycles (or rounds of sweeps) and their seconds */
+  double copy_bytes, copy_s;    /* bytes copied in and out by the copy thread and the seconds it spent copying */
 } stencil_server_stats;
 
 int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_bytes, int sweeps_per_round,

@@ -68,7 +68,7 @@ class stencil_server_stats(ctypes.Structure):
                 ("busy_s", ctypes.c_double), ("glups", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t),
                 ("hbm_peak", ctypes.c_size_t), ("queue_depth", ctypes.c_int), ("active", ctypes.c_int),
                 ("smooth_lup", ctypes.c_double), ("smooth_s", ctypes.c_double), ("solve_cycles", ctypes.c_double),
-                ("solve_s", ctypes.c_double)]
+                ("solve_s", ctypes.c_double), ("copy_bytes", ctypes.c_double), ("copy_s", ctypes.c_double)]
 
 
 class stencil_probe_result(ctypes.Structure):

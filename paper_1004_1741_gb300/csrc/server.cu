@@ -133,12 +133,16 @@ static bool copy_step(stencil_server* s) {
     }
   }
   if (down.empty() && admit.empty()) return false;
+  const auto tc0 = Clock::now();
+  double nbytes = 0.0;
   cudaStream_t cs = s->cstream;
   for (Req* q : down) {
     const size_t n = (size_t)(q->r.dims[0] + 2) * (size_t)(q->r.dims[1] + 2) * (size_t)(q->r.dims[2] + 2);
     const size_t esz = q->r.dtype == STENCIL_F64 ? 8 : 4;
-    if (q->r.u_out && q->du && (q->res.status == STENCIL_OK || q->res.status == STENCIL_ERR_NOT_CONVERGED))
+    if (q->r.u_out && q->du && (q->res.status == STENCIL_OK || q->res.status == STENCIL_ERR_NOT_CONVERGED)) {
       cudaMemcpyAsync(q->r.u_out, q->du, n * esz, cudaMemcpyDeviceToHost, cs);
+      nbytes += (double)(n * esz);
+    }
     if (q->du) cudaFreeAsync(q->du, cs);
     if (q->df) cudaFreeAsync(q->df, cs);
   }
@@ -149,6 +153,7 @@ static bool copy_step(stencil_server* s) {
     if (e == cudaSuccess && q->r.f_in) e = cudaMallocFromPoolAsync(&q->df, n * esz, s->pool, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(q->du, q->r.u_in, n * esz, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess && q->df) e = cudaMemcpyAsync(q->df, q->r.f_in, n * esz, cudaMemcpyHostToDevice, cs);
+    nbytes += (double)(n * esz) * (q->df ? 2.0 : 1.0);
     if (e != cudaSuccess) {
       cudaGetLastError();
       q->failed = true;
@@ -156,6 +161,8 @@ static bool copy_step(stencil_server* s) {
   }
   cudaStreamSynchronize(cs);  // downloads landed, uploads on the device
   std::lock_guard<std::mutex> lk(s->mu);
+  s->st.copy_bytes += nbytes;
+  s->st.copy_s += std::chrono::duration<double>(Clock::now() - tc0).count();
   for (Req* q : down) {
     q->du = q->df = nullptr;
     s->in_use -= q->bytes;
