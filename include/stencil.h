@@ -390,21 +390,24 @@ void stencil_server_destroy(stencil_server* srv);
 /* Self-check of the integer-arithmetic binary64 addition and multiplication:
  * n pairs drawn from a counter-based generator seeded by `seed` (random
  * magnitudes, ties, carries, zeros, signs), each summed on the integer pipes
- * (the symmetric form, and the ordered form in both argument orders) and
- * multiplied in integer arithmetic (both orders, random signs), against the
- * FP64 pipe.  *out_mismatch (host) receives the number of results whose bits
- * differ (must be 0), *out_fast the number of pairs the symmetric addition
- * handled.  Blocking. */
+ * (the symmetric form, the ordered form in both argument orders, and the
+ * any-sign form in both orders with random signs) and multiplied in integer
+ * arithmetic (both orders, random signs), against the FP64 pipe.
+ * *out_mismatch (host) receives the number of results whose bits differ (must
+ * be 0), *out_fast the number of pairs the symmetric addition handled and,
+ * when out_fast_any is not NULL, *out_fast_any the number the any-sign
+ * addition handled.  Blocking. */
 int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t seed, uint64_t* out_mismatch,
-                             uint64_t* out_fast);
+                             uint64_t* out_fast, uint64_t* out_fast_any);
 
 /* Throughput probes (not in the paper; they measure the roofline's
  * denominators on the GPU at hand): whole-GPU rates of FP64 additions (the
  * smoothers' FMA-form addition, one rounding each), FP32 additions, 32-bit
  * integer ALU instructions (lop3), binary64 additions carried out on the
  * integer pipes (the smoothers' ordered integer-pipe addition on operands in
- * its fast path; int_add_fast_fraction must be 1), each from 8 independent
- * dependency chains per thread at 32 warps per SM; and, when copy_bytes >= 32,
+ * its fast path; int_add_fast_fraction must be 1), the any-sign integer-pipe
+ * addition on operands of unlike signs, each from 8 independent dependency
+ * chains per thread at 32 warps per SM; and, when copy_bytes >= 32,
  * the DRAM bandwidth of a 16-byte-vector copy kernel over copy_bytes of
  * workspace (read + write bytes per second).  sm_count and clock_khz are the
  * device's (cudaDevAttrClockRate: the maximum SM clock).  Blocking; changes
@@ -415,6 +418,7 @@ typedef struct stencil_probe_result {
   double alu_ops_per_s;
   double int_add_f64_per_s;
   double int_add_fast_fraction;
+  double int_add_any_f64_per_s;
   double copy_bytes_per_s;
   int sm_count;
   int clock_khz;

@@ -74,7 +74,8 @@ class stencil_server_stats(ctypes.Structure):
 class stencil_probe_result(ctypes.Structure):
     _fields_ = [("fp64_ops_per_s", ctypes.c_double), ("fp32_ops_per_s", ctypes.c_double),
                 ("alu_ops_per_s", ctypes.c_double), ("int_add_f64_per_s", ctypes.c_double),
-                ("int_add_fast_fraction", ctypes.c_double), ("copy_bytes_per_s", ctypes.c_double),
+                ("int_add_fast_fraction", ctypes.c_double), ("int_add_any_f64_per_s", ctypes.c_double),
+                ("copy_bytes_per_s", ctypes.c_double),
                 ("sm_count", ctypes.c_int), ("clock_khz", ctypes.c_int)]
 
 
@@ -116,7 +117,7 @@ _SIGS = {
     "stencil_server_stats_get": (_I, [_P, ctypes.POINTER(stencil_server_stats)]),
     "stencil_server_destroy": (None, [_P]),
     "stencil_selftest_int_add": (_I, [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64),
-                                      ctypes.POINTER(ctypes.c_uint64)]),
+                                      ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "residual_norm_noalloc": (_I, [_P, _P, _I64P, _D, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "stencil_solve_mixed": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
     "stencil_solve_f64": (_I, [_P, _P, _P, _I64P, _D, _I, _D, _I, _I, _PP, ctypes.POINTER(_D), ctypes.POINTER(_I),
@@ -328,12 +329,13 @@ def stencil_batched(ctx: Context, us, fs, hs, nsweeps, smoother: int, *, nt: int
     _check(ctx, rc)
 
 
-def stencil_selftest_int_add(ctx: Context, n: int, seed: int = 1):
-    """Returns (mismatches, handled on the integer pipes) over n generated pairs."""
-    mm, fast = ctypes.c_uint64(0), ctypes.c_uint64(0)
+def stencil_selftest_int_add(ctx: Context, n: int, seed: int = 1, with_any: bool = False):
+    """Returns (mismatches, pairs the symmetric integer-pipe addition handled) over n generated
+    pairs, and also the pairs the any-sign addition handled when with_any."""
+    mm, fast, fast_any = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
     _check(ctx, load_library().stencil_selftest_int_add(ctx.handle, int(n), int(seed), ctypes.byref(mm),
-                                                        ctypes.byref(fast)))
-    return mm.value, fast.value
+                                                        ctypes.byref(fast), ctypes.byref(fast_any)))
+    return (mm.value, fast.value, fast_any.value) if with_any else (mm.value, fast.value)
 
 
 def stencil_set_wait_limit(ctx: Context, timeout_ns: int, never_publish: int = -1) -> None:

@@ -26,6 +26,7 @@ struct ArithF64 {
   static __device__ __forceinline__ double f_term(double hh, double fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ double add_k(double a, double b) { return add(a, b); }
+  static __device__ __forceinline__ double add_f(double a, double b) { return add(a, b); }
 };
 
 struct ArithF64Fma {
@@ -43,6 +44,7 @@ struct ArithF64Fma {
   static __device__ __forceinline__ double mul_b(double b, double s) { return mul(b, s); }
   template <int K>
   static __device__ __forceinline__ double add_k(double a, double b) { return add(a, b); }
+  static __device__ __forceinline__ double add_f(double a, double b) { return add(a, b); }
 };
 
 struct ArithF32 {
@@ -52,6 +54,7 @@ struct ArithF32 {
   static __device__ __forceinline__ float f_term(float hh, float fv) { return mul(hh, fv); }
   template <int K>
   static __device__ __forceinline__ float add_k(float a, float b) { return add(a, b); }
+  static __device__ __forceinline__ float add_f(float a, float b) { return add(a, b); }
 };
 
 // Binary64 addition carried out on the integer pipes.
@@ -120,6 +123,52 @@ __device__ __forceinline__ bool int_add_f64_ge(double a, double b, double* out) 
   return true;
 }
 
+// Binary64 addition of operands of any signs on the integer pipes: the
+// IEEE-754 round-to-nearest-even sum whenever the operand of larger magnitude
+// has exponent field 1..2045 and the sum is zero or normal (both operands zero
+// included); otherwise it reports failure and the caller uses the FP64 pipe.
+// Method: order the operands by magnitude; the larger significand (implicit
+// bit at 62) and the smaller one, shifted right by the exponent gap with the
+// bits shifted out ORed into bit 0 (a sticky bit), are added or subtracted in
+// 64 bits.  The ten bits below the rounding position keep the result on the
+// right side of every rounding boundary: the sticky bit makes the computed
+// value odd and off the true one by less than one unit of bit 0, while every
+// boundary (and every tie) is a multiple of 2^8 there; a subtraction with a gap
+// of two or more normalises by at most one bit, and one with a gap of at most
+// one loses no bit at all.  The result is normalised to bit 62 (a carry into
+// bit 63 folds back by one right shift, the dropped bit ORed into bit 0) and
+// rounded at bit 10 as in int_add_f64; an exact zero difference is +0.
+__device__ __forceinline__ bool int_add_f64_any(double a, double b, double* out) {
+  const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+  const unsigned long long MAG = 0x7FFFFFFFFFFFFFFFull, FRAC = 0xFFFFFFFFFFFFFull;
+  const bool sw = (B & MAG) > (A & MAG);
+  const unsigned long long H = sw ? B : A, L = sw ? A : B;
+  const unsigned eh = (unsigned)(H >> 52) & 0x7FFu, el = (unsigned)(L >> 52) & 0x7FFu;
+  if (eh - 1u >= 2045u) {  // the larger operand is zero, subnormal or too large
+    if ((H & MAG) != 0ull) return false;
+    *out = __longlong_as_double((long long)(A & B));  // two zeros: -0 only when both are -0
+    return true;
+  }
+  const unsigned long long MH = ((H & FRAC) | (1ull << 52)) << 10;
+  const unsigned long long ML0 = ((L & FRAC) | (el ? (1ull << 52) : 0ull)) << 10;  // a subnormal has no implicit bit
+  const unsigned d = min(eh - max(el, 1u), 63u);                                   // ... and exponent 1
+  const unsigned long long ML = (ML0 >> d) | (unsigned long long)((ML0 & ((1ull << d) - 1ull)) != 0ull);
+  const unsigned long long D = ((A ^ B) >> 63) ? MH - ML : MH + ML;
+  if (D == 0ull) {
+    *out = 0.0;
+    return true;
+  }
+  const int lz = __clzll((long long)D);
+  const int e = (int)eh + 1 - lz;  // exponent field of the normalised sum
+  if (e < 1) return false;
+  const unsigned long long D2 = lz == 0 ? (D >> 1) | (D & 1ull) : D << (lz - 1);
+  const unsigned long long R = D2 + (0x1FFull + ((D2 >> 10) & 1ull));
+  const unsigned long long res = (R >> 10) + ((unsigned long long)(e - 1) << 52);
+  *out = __longlong_as_double((long long)(res | (H & ~MAG)));
+  return true;
+}
+
 // Binary64 multiplication carried out in integer arithmetic (the 64-bit
 // products on the integer multiply-add path, the rest on the ALU pipe): the
 // IEEE round-to-nearest-even product when both operands are normal and the
@@ -175,6 +224,7 @@ struct ArithF64Mix {
     if (K == 0 ? int_add_f64(a, b, &r) : int_add_f64_ge(a, b, &r)) return r;
     return ArithF64Fma::add(a, b);
   }
+  static __device__ __forceinline__ double add_f(double a, double b) { return add(a, b); }
 };
 
 // The arithmetic A for a sweep whose f array already holds the products
@@ -232,7 +282,7 @@ __device__ __forceinline__ T site_update(T w, T e, T s, T n, T bo, T t, T fv, T 
   acc = Ar::template add_k<2>(acc, n);
   acc = Ar::template add_k<3>(acc, bo);
   acc = Ar::template add_k<4>(acc, t);
-  if (HAS_F) acc = Ar::add(acc, Ar::f_term(c.hh, fv));
+  if (HAS_F) acc = Ar::add_f(acc, Ar::f_term(c.hh, fv));
   T v = Ar::mul_b(c.b, acc);
   if (WEIGHTED) v = Ar::add(Ar::mul(c.a, uc), v);
   return v;

@@ -97,6 +97,29 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_int_add_kernel(int iters,
   atomicAdd(out_fast, (unsigned long long)fast);
 }
 
+// The any-sign integer-pipe addition (common.cuh int_add_f64_any) on pairs of
+// unlike signs: each chain adds a small value of alternating sign to a running
+// value of about 1 and resets the exponent as above, so every addition is a
+// true subtraction or addition of magnitudes and none leaves the fast path.
+__global__ void __launch_bounds__(PROBE_THREADS) probe_int_add_any_kernel(int iters, double* __restrict__ out) {
+  double v[PROBE_CH];
+  const double b = 0.001 * (1.0 + threadIdx.x * 1e-3);
+#pragma unroll
+  for (int c = 0; c < PROBE_CH; ++c) v[c] = (c & 1) ? -(1.0 + 1e-3 * c) : 1.0 + 1e-3 * c;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < PROBE_CH; ++c) {
+      double r;
+      if (!int_add_f64_any(v[c], (it & 1) ? b : -b, &r)) r = ArithF64Fma::add(v[c], b);
+      v[c] = __hiloint2double((__double2hiint(r) & 0x80000000) | 0x3FF00000, __double2loint(r));
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < PROBE_CH; ++c) s = __dadd_rn(s, v[c]);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // Device-to-device copy of n 16-byte vectors (grid-stride): DRAM read + write bandwidth.
 __global__ void __launch_bounds__(PROBE_THREADS) probe_copy_kernel(const double2* __restrict__ src,
                                                                    double2* __restrict__ dst, size_t n) {
@@ -158,6 +181,10 @@ extern "C" int stencil_probe_throughput(stencil_ctx* ctx, size_t copy_bytes, ste
   const double adds = (double)nthr * PROBE_CH * iters_add;
   out->int_add_f64_per_s = t > 0 ? adds / t : 0.0;
   out->int_add_fast_fraction = fast / (2.0 * adds);  // warm-up and timed launch both counted
+  if (e == cudaSuccess) {
+    t = timed([&] { probe_int_add_any_kernel<<<blocks, PROBE_THREADS>>>(iters_add, (double*)scratch); });
+    out->int_add_any_f64_per_s = t > 0 ? adds / t : 0.0;
+  }
   if (e == cudaSuccess && copy_bytes >= 32) {
     const size_t n = copy_bytes / 2 / sizeof(double2);
     double2* buf = (double2*)ws_get(ctx, SLOT_JACOBI_TMP, 2 * n * sizeof(double2), &status);

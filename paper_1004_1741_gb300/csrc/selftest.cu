@@ -1,6 +1,7 @@
-// Self-check of the integer-pipe binary64 additions (common.cuh int_add_f64 and
-// its ordered form int_add_f64_ge) and of the integer-arithmetic multiplication
-// (int_mul_f64) against the FP64 pipe on generated operand pairs.
+// Self-check of the integer-pipe binary64 additions (common.cuh int_add_f64,
+// its ordered form int_add_f64_ge and the any-sign form int_add_f64_any) and
+// of the integer-arithmetic multiplication (int_mul_f64) against the FP64
+// pipe on generated operand pairs.
 #include "internal.h"
 
 namespace stn {
@@ -34,7 +35,7 @@ __device__ __forceinline__ double gen_operand(unsigned long long r, unsigned lon
 
 __global__ void selftest_int_add_kernel(unsigned long long n, unsigned long long seed,
                                         unsigned long long* __restrict__ counts) {
-  unsigned long long mism = 0, fast = 0;
+  unsigned long long mism = 0, fast = 0, fast_any = 0;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long r0 = mix64(seed ^ (4 * i)), r1 = mix64(seed ^ (4 * i + 1));
@@ -56,11 +57,18 @@ __global__ void selftest_int_add_kernel(unsigned long long n, unsigned long long
     if (int_add_f64_ge(b, a, &em) && __double_as_longlong(em) != __double_as_longlong(__dadd_rn(b, a))) ++mism;
     // the integer-path multiplication, on the same pair with independent random signs
     const double sa = ((r3 >> 17) & 1ull) ? -a : a, sb = ((r3 >> 18) & 1ull) ? -b : b;
+    // the any-sign addition, on the pair with those signs, in both argument orders
+    if (int_add_f64_any(sa, sb, &em)) {
+      ++fast_any;
+      if (__double_as_longlong(em) != __double_as_longlong(__dadd_rn(sa, sb))) ++mism;
+    }
+    if (int_add_f64_any(sb, sa, &em) && __double_as_longlong(em) != __double_as_longlong(__dadd_rn(sb, sa))) ++mism;
     if (int_mul_f64(sa, sb, &em) && __double_as_longlong(em) != __double_as_longlong(__dmul_rn(sa, sb))) ++mism;
     if (int_mul_f64(sb, sa, &em) && __double_as_longlong(em) != __double_as_longlong(__dmul_rn(sb, sa))) ++mism;
   }
   atomicAdd(counts, mism);
   atomicAdd(counts + 1, fast);
+  atomicAdd(counts + 2, fast_any);
 }
 
 }  // namespace stn
@@ -68,7 +76,7 @@ __global__ void selftest_int_add_kernel(unsigned long long n, unsigned long long
 using namespace stn;
 
 extern "C" int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t seed, uint64_t* out_mismatch,
-                                        uint64_t* out_fast) {
+                                        uint64_t* out_fast, uint64_t* out_fast_any) {
   if (!ctx || !out_mismatch || !out_fast) return STENCIL_ERR_ARG;
   ctx->err.clear();
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -76,8 +84,8 @@ extern "C" int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t s
   int status;
   unsigned long long* d = (unsigned long long*)ws_get(ctx, SLOT_RED_RESULT, 4 * sizeof(double), &status);
   if (!d) return status;
-  unsigned long long h[2] = {0, 0};
-  e = cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+  unsigned long long h[3] = {0, 0, 0};
+  e = cudaMemset(d, 0, sizeof(h));
   if (e == cudaSuccess) {
     selftest_int_add_kernel<<<ctx->sm_count * 8, 256>>>((unsigned long long)n, (unsigned long long)seed, d);
     ctx->launches++;
@@ -87,5 +95,6 @@ extern "C" int stencil_selftest_int_add(stencil_ctx* ctx, uint64_t n, uint64_t s
   if (e != cudaSuccess) return cuda_err(ctx, e, "selftest_int_add");
   *out_mismatch = h[0];
   *out_fast = h[1];
+  if (out_fast_any) *out_fast_any = h[2];
   return STENCIL_OK;
 }

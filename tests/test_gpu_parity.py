@@ -286,11 +286,13 @@ def test_gs_laplace_config1(ctx):
 
 # ------------------------------------------ FP64 additions on the integer pipes --
 def test_int_add_selftest(ctx):
-    """The integer-pipe binary64 addition equals the FP64 pipe on 2^26 generated pairs
-    (random magnitudes, near-equal operands with ties and carries, raw bit patterns)."""
-    mism, fast = capi.stencil_selftest_int_add(ctx, 1 << 26, seed=12345)
+    """The integer-pipe binary64 additions equal the FP64 pipe on 2^26 generated pairs
+    (random magnitudes, near-equal operands with ties and carries, raw bit patterns; random
+    signs and both argument orders for the any-sign form)."""
+    mism, fast, fast_any = capi.stencil_selftest_int_add(ctx, 1 << 26, seed=12345, with_any=True)
     assert mism == 0
     assert fast > (1 << 24)
+    assert fast_any > (1 << 25)
 
 
 @pytest.mark.parametrize("int_adds", [1, 2, 3, 4, 5])
@@ -658,7 +660,7 @@ def test_throughput_probe(ctx):
     r = capi.stencil_probe_throughput(ctx, copy_bytes=1 << 30)
     assert r["int_add_fast_fraction"] == 1.0
     assert r["fp64_ops_per_s"] > 1e11 and r["fp32_ops_per_s"] > r["fp64_ops_per_s"]
-    assert r["alu_ops_per_s"] > r["int_add_f64_per_s"] > 0
+    assert r["alu_ops_per_s"] > r["int_add_f64_per_s"] > r["int_add_any_f64_per_s"] > 0
     assert 5e11 < r["copy_bytes_per_s"] < 2e13
     assert r["sm_count"] > 0 and r["clock_khz"] > 0
 
