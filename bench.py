@@ -505,9 +505,9 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
     """The headline step end to end through the C ABI: every step copies both grids in from pinned host
     memory, runs the two smoothers, computes both residual norms and copies both grids back.  The steps are
     pipelined over two sets of device grids and three streams: step k+1's grids are copied in while step k
-    computes, and step k's results are copied out while step k+1 computes (the kernels themselves run one
-    after the other on the compute stream, as in the device-timed step).  Timed from the first copy in to
-    the last copy out."""
+    computes (issued after step k's Jacobi call, before its blocking persistent Gauss-Seidel call), and step
+    k's results are copied out while step k+1 computes (the kernels themselves run one after the other on the
+    compute stream, as in the device-timed step).  Timed from the first copy in to the last copy out."""
     import numpy as np
 
     hj = torch.from_numpy(u_host).pin_memory()
@@ -524,7 +524,7 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
     ev_out = [torch.cuda.Event() for _ in range(2)]
     used = [False, False]
 
-    def step(k):
+    def copy_in(k):
         b = k % 2
         with torch.cuda.stream(s_in):
             if used[b]:
@@ -532,9 +532,14 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
             dj[b].copy_(hj, non_blocking=True)
             dg[b].copy_(hg, non_blocking=True)
             ev_in[b].record(s_in)
+
+    def run(k, prefetch):
+        b = k % 2
         s_run.wait_event(ev_in[b])
         capi.stencil_jacobi(ctx, dj[b], None, 1.0, SWEEPS, nt=cj["nt"], tile=cj["tile"], variant=cj["variant"],
                             int_adds=cj["int_adds"], stream=s_run)
+        if prefetch:  # the next step's grids go in now: the persistent Gauss-Seidel call returns when it is done
+            copy_in(k + 1)
         capi.stencil_gs_lex(ctx, dg[b], None, 1.0, SWEEPS, nt=cg["nt"], tile=cg["tile"], variant=cg["variant"],
                             int_adds=cg["int_adds"], stream=s_run)
         capi.residual_norm(ctx, dj[b], None, 1.0, stream=s_run)
@@ -547,14 +552,16 @@ def run_e2e(ctx, capi, torch, u_host, dev, stream, args):
             ev_out[b].record(s_out)
         used[b] = True
 
-    for k in range(2):  # warm-up: workspace, plans, graphs
-        step(k)
+    copy_in(0)  # warm-up: workspace, plans, graphs
+    for k in range(2):
+        run(k, k == 0)
     torch.cuda.synchronize()
     a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = max(1, min(args.steps, 10))
     a.record(s_in)
+    copy_in(0)
     for k in range(steps):
-        step(k)
+        run(k, k + 1 < steps)
     s_in.wait_stream(s_out)
     b_.record(s_in)
     torch.cuda.synchronize()
@@ -772,8 +779,8 @@ def run_suite_served(args):
     rounded to multiples of 16, solve requests one less so that their multigrid levels nest; 10-200 sweeps,
     or a solve to 1e-8 capped at 2000 fine-grid sweeps; FP64/FP32 smoothing), 150 GB HBM budget, for a range
     of arrival rates; p50/p99 latency, GLUP/s, admitted/cancelled per rate.  At most --slots requests are on
-    the device at once; at the end of the arrival window the requests never admitted are cancelled (counted)
-    and the admitted ones drain.  Beside it, the same streams served one request at a time through the plain
+    the device at once; --grace seconds after the end of the arrival window the requests never admitted are
+    cancelled (counted) and the admitted ones drain.  Host inputs and result buffers are page-locked.  Beside it, the same streams served one request at a time through the plain
     single-grid calls (copy in, smooth or multigrid-solve, copy out), first come first served: the per-request
     baseline."""
     import numpy as np
@@ -785,6 +792,16 @@ def run_suite_served(args):
     window = args.window
     pool = {}
 
+    def pinned(a):
+        """a copy of a in page-locked host memory (the copies of both arms run at the link's rate)"""
+        t = torch.empty(a.shape, dtype=torch.float64 if a.dtype == np.float64 else torch.float32, pin_memory=True)
+        out = t.numpy()
+        out[...] = a
+        keep.append(t)
+        return out
+
+    keep = []
+
     def inputs(nn, dt):
         key = (nn, dt)
         if key not in pool:
@@ -793,7 +810,7 @@ def run_suite_served(args):
             u[1:-1, 1:-1, 1:-1] = 0.0
             fz = np.zeros_like(u)
             fz[1:-1, 1:-1, 1:-1] = rng.standard_normal((nn,) * 3)
-            pool[key] = (np.ascontiguousarray(u.astype(dt)), np.ascontiguousarray(fz.astype(dt)))
+            pool[key] = (pinned(u.astype(dt)), pinned(fz.astype(dt)))
         return pool[key]
 
     def shape(r):
@@ -809,11 +826,24 @@ def run_suite_served(args):
     def pct(lat, q):
         return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))] if lat else None
 
+    def prepare(reqs):
+        """the stream's host buffers, page-locked before the clock starts: inputs per shape, and one
+        result buffer per shape (what the copy back costs, without a buffer per request; the values
+        are not used)"""
+        for r in reqs:
+            if r.arrival_s > window:
+                break
+            nn, dt = shape(r)
+            u, _ = inputs(nn, dt)
+            if (nn, dt) not in outs:
+                outs[(nn, dt)] = pinned(np.empty_like(u))
+
     def served(reqs):
+        prepare(reqs)
         with capi.Server(0, hbm_budget_bytes=150 * 10 ** 9, sweeps_per_round=args.quantum,
                          max_active=args.slots) as srv:
             t0 = time.perf_counter()
-            tickets = []
+            tickets, late = [], []
             for r in reqs:
                 if r.arrival_s > window:
                     break
@@ -822,21 +852,26 @@ def run_suite_served(args):
                     time.sleep(r.arrival_s - now)
                 nn, dt = shape(r)
                 u, fz = inputs(nn, dt)
-                # results are read back into one host buffer per shape (what the copy costs, without
-                # holding a buffer per request; the values are not used)
-                outbuf = outs.setdefault((nn, dt), np.empty_like(u))
+                late.append(time.perf_counter() - t0 - r.arrival_s)  # the server's latency starts at submit
                 tickets.append(srv.submit(kinds[r.kind], u, fz, 1.0 / (nn + 1), r.sweeps, rtol=r.rtol,
-                                          u_out=outbuf))
+                                          u_out=outs[(nn, dt)]))
             t_arr = time.perf_counter() - t0
-            for t in tickets:  # end of the window: what was never admitted is cancelled, admitted work drains
+            time.sleep(args.grace)  # requests that arrived just before the window closed get admitted
+            for t in tickets:  # then what was never admitted is cancelled, admitted work drains
                 srv.cancel(t)
             results = [srv.wait(t, args.drain) for t in tickets]
             t_end = time.perf_counter() - t0
             st = srv.stats()
         if any(r is None for r in results):
             raise RuntimeError("served requests did not drain within %.0f s" % args.drain)
-        done = [r for r in results if r["status"] in (capi.STENCIL_OK, capi.STENCIL_ERR_NOT_CONVERGED)]
-        lat = sorted(r["latency_s"] for r in done)
+        ok = (capi.STENCIL_OK, capi.STENCIL_ERR_NOT_CONVERGED)
+        # latency from the scheduled arrival, like the one-at-a-time baseline's
+        lat = sorted(r["latency_s"] + lt for r, lt in zip(results, late) if r["status"] in ok)
+        done = [r for r in results if r["status"] in ok]
+        # the last result's completion, from the stream's start (the grace wait and the drain's polling
+        # are not work)
+        t_last = max([reqs[i].arrival_s + lt + r["latency_s"] for i, (r, lt) in enumerate(zip(results, late))
+                      if r["status"] in ok] or [t_end])
         return {"submitted": len(tickets), "completed": len(done),
                 "cancelled": sum(1 for r in results if r["status"] == capi.STENCIL_ERR_CANCELLED),
                 "solves_converged": sum(1 for r in results if r["status"] == capi.STENCIL_OK and r["rel_residual"] >= 0),
@@ -844,14 +879,15 @@ def run_suite_served(args):
                 "smoothing_glups": st["smooth_lup"] / st["smooth_s"] / 1e9 if st["smooth_s"] > 0 else None,
                 "solve_cycles": st["solve_cycles"], "solve_s": st["solve_s"], "smoothing_s": st["smooth_s"],
                 "copy_gb": st["copy_bytes"] / 1e9, "copy_s": st["copy_s"],
-                "glups_wall": st["lup_total"] / t_end / 1e9, "lup": st["lup_total"], "busy_s": st["busy_s"],
-                "wall_s": t_end, "arrival_window_s": t_arr, "hbm_peak_gb": st["hbm_peak"] / 1e9,
+                "glups_wall": st["lup_total"] / t_last / 1e9, "lup": st["lup_total"], "busy_s": st["busy_s"],
+                "wall_s": t_last, "arrival_window_s": t_arr, "hbm_peak_gb": st["hbm_peak"] / 1e9,
                 "launches": st["launches"]}
 
     def plain(reqs):
         """The same arrivals, one request at a time (FIFO) through the single-grid calls."""
         ctx = capi.Context(0)
         dev = torch.device("cuda", 0)
+        prepare(reqs)
         t0 = time.perf_counter()
         lat, lup, n = [], 0.0, 0
         t_smooth, lup_smooth, t_copy = 0.0, 0.0, 0.0
@@ -884,7 +920,7 @@ def run_suite_served(args):
                 lup_smooth += float(r.sweeps) * nn ** 3
             torch.cuda.synchronize()
             tc = time.perf_counter()
-            u.cpu()
+            torch.from_numpy(outs[(nn, dt)]).copy_(u)
             t_copy += time.perf_counter() - tc
             lat.append(time.perf_counter() - t0 - r.arrival_s)
             n += 1
@@ -936,12 +972,14 @@ def main():
     ap.add_argument("--inner", type=int, default=1, help="FP32 V-cycles per outer iteration (--suite mixed)")
     ap.add_argument("--suite", choices=["mixed", "served", "mg"], help="a secondary workload instead of the headline")
     ap.add_argument("--rates", default="2,5,10,25,50,100,200,500,2000")
-    ap.add_argument("--plain-max-rate", type=float, default=50.0,
+    ap.add_argument("--plain-max-rate", type=float, default=500.0,
                     help="--suite served: rates up to this also run the one-request-at-a-time baseline")
     ap.add_argument("--window", type=float, default=3.0)
     ap.add_argument("--drain", type=float, default=60.0)
-    ap.add_argument("--slots", type=int, default=32)
-    ap.add_argument("--quantum", type=int, default=10, help="--suite served: sweeps per request and round")
+    ap.add_argument("--grace", type=float, default=0.5,
+                    help="--suite served: seconds after the window before unadmitted requests are cancelled")
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--quantum", type=int, default=50, help="--suite served: sweeps per request and round")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

@@ -1,5 +1,6 @@
 // Shared device helpers of the GB300 stencil library (product path only).
 #pragma once
+#include <type_traits>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -302,6 +303,15 @@ __device__ __forceinline__ T site_update_warp(bool active, T w, T e, T s, T n, T
     return active ? site_update<T, typename Ar::Mixed, HAS_F, WEIGHTED>(w, e, s, n, bo, t, fv, uc, c) : T(0);
   } else {
     return active ? site_update<T, Ar, HAS_F, WEIGHTED>(w, e, s, n, bo, t, fv, uc, c) : T(0);
+  }
+}
+
+// f(std::integral_constant<int, I>{}) for I = 0..N-1, unrolled at compile time.
+template <int N, int I = 0, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<N, I + 1>(f);
   }
 }
 

@@ -192,6 +192,30 @@ static bool copy_step(stencil_server* s) {
   return true;
 }
 
+// Requests finished on the device (state 2) leave the active list for the copy
+// thread, which reads them back.  handoff_locked: the caller holds s->mu.
+static void handoff_locked(stencil_server* s) {
+  std::vector<uint64_t> keep;
+  bool any = false;
+  for (uint64_t t : s->active) {
+    Req* q = s->reqs[t];
+    if (q->state == 2) {
+      q->state = 4;
+      s->to_download.push_back(t);
+      any = true;
+    } else {
+      keep.push_back(t);
+    }
+  }
+  s->active.swap(keep);
+  if (any) s->cv_copy.notify_all();
+}
+
+static void handoff_finished(stencil_server* s) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  handoff_locked(s);
+}
+
 // --- compute thread: one round over the requests on the device --------------
 //
 // Smoothing requests: up to `quantum` sweeps each, all requests of one
@@ -250,6 +274,7 @@ static bool compute_round(stencil_server* s) {
   cudaStreamSynchronize(st);
   const auto t1 = Clock::now();
   smooth_lup = lup;
+  handoff_finished(s);  // finished smoothing requests go back before the solve cycles run
   for (Req* q : act) {
     if (q->r.kind != STENCIL_REQ_SOLVE) continue;
     const bool odd = q->r.dims[0] % 2 && q->r.dims[1] % 2 && q->r.dims[2] % 2 && q->r.dims[0] >= 3 &&
@@ -295,18 +320,7 @@ static bool compute_round(stencil_server* s) {
   s->st.smooth_s += std::chrono::duration<double>(t1 - t0).count();
   s->st.solve_cycles += cycles;
   s->st.solve_s += std::chrono::duration<double>(t2 - t1).count();
-  std::vector<uint64_t> keep;
-  for (uint64_t t : s->active) {
-    Req* q = s->reqs[t];
-    if (q->state == 2) {  // finished on the device: to the copy thread
-      q->state = 4;
-      s->to_download.push_back(t);
-    } else {
-      keep.push_back(t);
-    }
-  }
-  s->active.swap(keep);
-  s->cv_copy.notify_all();
+  handoff_locked(s);
   return true;
 }
 
