@@ -33,7 +33,7 @@ SWEEPS = 100
 # default, the adaptive form, pays a warp vote per update for data of both signs)
 HEADLINE = {
     "jacobi": {"nt": 1, "tile": (32, 4, 0), "variant": 0, "int_adds": 3},
-    "gs": {"nt": 1, "tile": (8, 16, 0), "variant": 5, "int_adds": 2},
+    "gs": {"nt": 1, "tile": (8, 16, 0), "variant": 5, "int_adds": 3},
 }
 NT_SWEEP = [1, 2, 4, 8, 16]
 METRIC = "GLUP/s at 400^3 FP64 (Jacobi, GS) vs HBM roofline; batched/served vs plain, p99"

@@ -306,15 +306,6 @@ __device__ __forceinline__ T site_update_warp(bool active, T w, T e, T s, T n, T
   }
 }
 
-// f(std::integral_constant<int, I>{}) for I = 0..N-1, unrolled at compile time.
-template <int N, int I = 0, class F>
-__device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (I < N) {
-    f(std::integral_constant<int, I>{});
-    static_for<N, I + 1>(f);
-  }
-}
-
 // Asynchronous element copy global -> shared (cp.async, through L1) and its
 // group bookkeeping: wait until at most N of this thread's groups are pending.
 template <typename T>

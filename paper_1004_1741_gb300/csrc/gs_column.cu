@@ -103,56 +103,37 @@ __device__ __forceinline__ void gs_column_body(T* u, const T* __restrict__ f, co
   // f: copied with the own row (plane t - j + 2 + PF, same slot), read at the update
   const T* gf = HAS_F ? f + (comp ? g.at(x, y, z0) : 0) + (int64_t)(ts - j + 2 + PF) * sy : nullptr;
   auto wrap = [](int s) { return s == R - 1 ? 0 : s + 1; };
-  // One step of the march.  STEADY: every duty's window holds t for every thread (no window tests);
-  // SC >= 0: t mod R == SC is known at compile time (the update's three slots are constants; st is
-  // then left alone, and is t mod R again after a whole number of ring periods).
-  auto step = [&](int t, auto steady, auto stc) {
-    constexpr bool S = decltype(steady)::value;
-    constexpr int SC = decltype(stc)::value;
-    const bool wl = S || inwin(t, lo_l, hi_l);
+  for (int t = ts; t <= te; ++t) {
+    const bool wl = inwin(t, lo_l, hi_l);
     if (ldo && wl) cp_async_elem(cell + sl * PL, go);
     if (ldx && wl) cp_async_elem(xcell + sx * PL, gx);
-    if (ldy && (S || inwin(t, lo_y, hi_y))) cp_async_elem(ycell + sl * PL, gy);
-    if (HAS_F && comp && (S || inwin(t, lo_f, hi_f))) cp_async_elem(fcell + sl * FPL, gf);
+    if (ldy && inwin(t, lo_y, hi_y)) cp_async_elem(ycell + sl * PL, gy);
+    if (HAS_F && comp && inwin(t, lo_f, hi_f)) cp_async_elem(fcell + sl * FPL, gf);
     cp_async_commit();
-    const int s0 = SC >= 0 ? SC : st;
-    const int sm1 = SC >= 0 ? (SC + R - 1) % R : (st == 0 ? R - 1 : st - 1);
-    const int sp1 = SC >= 0 ? (SC + 1) % R : wrap(st);
-    const bool upd = comp && (S || inwin(t, lo_c, hi_c));
-    const T* pm = cell + sm1 * PL;
-    const T* pp = cell + sp1 * PL;
     if constexpr (AdaptOf<Ar>::on) {  // the whole warp votes (t is uniform; every ring read stays in the ring)
-      const T fv = HAS_F ? fcell[s0 * FPL] : T(0);
+      const bool upd = comp && inwin(t, lo_c, hi_c);
+      const int sm1 = st == 0 ? R - 1 : st - 1, sp1 = wrap(st);
+      const T* pm = cell + sm1 * PL;
+      const T* pp = cell + sp1 * PL;
+      const T fv = HAS_F ? fcell[st * FPL] : T(0);
       const T v = site_update_warp<T, Ar, HAS_F, false>(upd, pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv, T(0),
                                                         c);
-      if (upd) cell[s0 * PL] = v;
-    } else if (upd) {
-      const T fv = HAS_F ? fcell[s0 * FPL] : T(0);
+      if (upd) cell[st * PL] = v;
+    } else if (comp && inwin(t, lo_c, hi_c)) {
+      const int sm1 = st == 0 ? R - 1 : st - 1, sp1 = wrap(st);
+      const T* pm = cell + sm1 * PL;
+      const T* pp = cell + sp1 * PL;
+      const T fv = HAS_F ? fcell[st * FPL] : T(0);
       const T v = site_update<T, Ar, HAS_F, false>(pm[-1], pp[1], pm[-RW], pp[RW], pm[0], pp[0], fv, T(0), c);
-      cell[s0 * PL] = v;
+      cell[st * PL] = v;
     }
-    if (comp && (S || inwin(t, lo_w, hi_w))) *gw = cell[sw * PL];
+    if (comp && inwin(t, lo_w, hi_w)) *gw = cell[sw * PL];
     if (HAS_F) gf += sy;
     cp_async_wait<PF>();
     __syncthreads();
-    sl = wrap(sl); sx = wrap(sx); sw = wrap(sw);
-    if (SC < 0) st = wrap(st);
+    sl = wrap(sl); sx = wrap(sx); sw = wrap(sw); st = wrap(st);
     go += sy; gx += sy; gy += sy; gw += sy;
-  };
-  using General = std::false_type;
-  using Steady = std::true_type;
-  using Runtime = std::integral_constant<int, -1>;
-  // Every window holds for t in [TX + TY, nzl - 4 - PF] (the latest first step is the write-back of
-  // row TY-1, the earliest last step the S row's copy); those steps run in whole ring periods from
-  // the first multiple of R in it, the rest as general steps.
-  const int t_u = ((TX + TY + R - 1) / R) * R;
-  const int nblk = nzl - 4 - PF >= t_u ? (nzl - 4 - PF - t_u + 1) / R : 0;
-  int t = ts;
-  if (nblk > 0) {
-    for (; t < t_u; ++t) step(t, General{}, Runtime{});
-    for (const int tb = t + nblk * R; t < tb; ++t) step(t, Steady{}, Runtime{});
   }
-  for (; t <= te; ++t) step(t, General{}, Runtime{});
   cp_async_wait<0>();
   __syncthreads();
 }
