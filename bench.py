@@ -442,16 +442,17 @@ def launch_counts(ctx, smoother, cfg):
 
 
 def _nt_cfg(name, nt):
-    """Launch parameters of one point of the temporal-depth sweep: the headline configuration at nt = 1;
-    Gauss-Seidel at nt = 2..4 as the persistent column march with nt sweeps per task (8x8 columns FP64 with
-    two integer-pipe additions, 16x8 FP32); deeper blocking and Jacobi at nt > 1 the library defaults."""
+    """Launch parameters of one point of the temporal-depth sweep: the FP64 headline configuration at nt = 1;
+    Gauss-Seidel at nt = 2..4 (and FP32 at nt = 1) as the persistent column march with nt sweeps per task
+    (8x8 columns FP64 with two integer-pipe additions, 16x8 FP32); deeper blocking, Jacobi at nt > 1 and FP32
+    Jacobi the library defaults."""
     base = HEADLINE["gs" if name.startswith("gs") else "jacobi"]
     f32 = name.endswith("f32")
     if name.startswith("gs") and nt <= 4:
         if nt == 1 and not f32:
             return dict(tile=base["tile"], variant=base["variant"], int_adds=base["int_adds"])
         return dict(tile=(16, 8, 0) if f32 else (8, 8, 0), variant=5, int_adds=-1 if f32 else 2)
-    if nt == 1:
+    if nt == 1 and not f32:
         return dict(tile=base["tile"], variant=base["variant"], int_adds=base["int_adds"])
     return dict(tile=(0, 0, 0), variant=0, int_adds=-1)
 
