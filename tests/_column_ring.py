@@ -128,49 +128,3 @@ def check_column_ring(tx: int, ty: int, nzl: int, pf: int, r: int | None = None)
     if len(written) != n:
         return "%d of %d sites written back" % (len(written), n)
     return None
-
-
-def f_ring_slots(pf: int) -> int:
-    """Slots of the per-thread ring of f: a value lives from its copy to its read pf + 1 steps later."""
-    return pf + 2
-
-
-def check_f_ring(tx: int, ty: int, nzl: int, pf: int, fr: int | None = None) -> str | None:
-    """The right-hand side's per-thread ring (gs_column.cu): thread (i, j) copies f of plane
-    t - i - j + pf + 1 (while in range) into its own slot t mod FR at step t, and its update of
-    plane t - i - j reads slot (t + 1) mod FR.  A copy issued at step s may land at any moment
-    until the end of step s + pf.  None when every update reads its own plane's f, landed, else
-    the first hazard."""
-    FR = f_ring_slots(pf) if fr is None else fr
-    ts = -3 - pf
-    te = nzl + tx + ty - 1
-    for j in range(ty):
-        for i in range(tx):
-            cell: dict[int, int] = {}  # slot -> plane it holds (landed)
-            inflight: list[tuple] = []  # (issue step, slot, plane)
-            reads = 0
-            for t in range(ts, te + 1):
-                kf = t - i - j + pf + 1
-                if 0 <= kf < nzl:
-                    slot = t % FR
-                    if any(s == slot for _, s, _ in inflight):
-                        return "thread %s step %d: copy into slot %d while another is in flight" % ((i, j), t, slot)
-                    inflight.append((t, slot, kf))
-                kk = t - i - j
-                if 0 <= kk < nzl:
-                    slot = (t + 1) % FR
-                    if any(s == slot for _, s, _ in inflight):
-                        return "thread %s step %d: reads slot %d while a copy into it may be in flight" % ((i, j), t, slot)
-                    if cell.get(slot) != kk:
-                        return "thread %s step %d: reads plane %s of f, needs %d" % ((i, j), t, cell.get(slot), kk)
-                    reads += 1
-                keep = []
-                for s, slot, k in inflight:
-                    if s <= t - pf:
-                        cell[slot] = k
-                    else:
-                        keep.append((s, slot, k))
-                inflight = keep
-            if reads != nzl:
-                return "thread %s read f %d times, %d planes" % ((i, j), reads, nzl)
-    return None
