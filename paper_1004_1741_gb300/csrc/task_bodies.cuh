@@ -87,23 +87,28 @@ __device__ __forceinline__ void jacobi_task_body(T* g_even, T* g_odd, const T* _
   const int64_t sx = g.sx, sy = g.sy;
   const int64_t base = g.at(X0, Y0, Z0);
   constexpr int NSITE = W * H * D;
+  static_assert(NSITE % 32 == 0, "whole warps of sites");
   for (int s = 0; s < ns; ++s) {
     const int v = p * tg.nt + s;
     const T* src = (v & 1) ? g_odd : g_even;
     T* dst = (v & 1) ? g_even : g_odd;
     const int64_t sb = base - (int64_t)s * (sy + sx + 1);
 #pragma unroll 2
-    for (int q = threadIdx.x; q < NSITE; q += GS_THREADS) {
+    for (int q = threadIdx.x; q < NSITE; q += GS_THREADS) {  // the same trip count for every lane of a warp
       const int ii = q % W, jj = (q / W) % H, kk = q / (W * H);
+      bool act = true;
       if (!full) {
         const int x = X0 - s + ii, y = Y0 - s + jj, z = Z0 - s + kk;
-        if (x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz) continue;
+        act = !(x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz);
       }
-      const int64_t o = sb + (int64_t)kk * sy + (int64_t)jj * sx + ii;
+      // a lane whose site lies outside the grid reads the first interior site instead (result discarded), so
+      // that the whole warp takes part in the adaptive arithmetic's vote
+      const int64_t o = act ? sb + (int64_t)kk * sy + (int64_t)jj * sx + ii : g.at(0, 0, 0);
       T fv = T(0);
       if (HAS_F) fv = f[o];
-      dst[o] = site_update<T, Ar, HAS_F, WEIGHTED>(src[o - 1], src[o + 1], src[o - sx], src[o + sx], src[o - sy],
-                                                   src[o + sy], fv, WEIGHTED ? src[o] : T(0), c);
+      const T val = site_update_warp<T, Ar, HAS_F, WEIGHTED>(act, src[o - 1], src[o + 1], src[o - sx], src[o + sx],
+                                                            src[o - sy], src[o + sy], fv, WEIGHTED ? src[o] : T(0), c);
+      if (act) dst[o] = val;
     }
     __syncthreads();
   }

@@ -48,15 +48,29 @@ static int tbj_levels(stencil_ctx* ctx, T* g_even, T* g_odd, const T* f, const G
   return STENCIL_OK;
 }
 
-template <typename T, int W, int H, int D>
-static int tbj_dispatch(stencil_ctx* ctx, T* g_even, T* g_odd, const T* f, const Geom& g, Coef<T> c,
-                        const TileGeom& tg, bool weighted, cudaStream_t st) {
-  using Ar = typename DefaultArith<T>::type;
+template <typename T, class Ar, int W, int H, int D>
+static int tbj_arith(stencil_ctx* ctx, T* g_even, T* g_odd, const T* f, const Geom& g, Coef<T> c,
+                     const TileGeom& tg, bool weighted, cudaStream_t st) {
   if (f)
     return weighted ? tbj_levels<T, Ar, true, true, W, H, D>(ctx, g_even, g_odd, f, g, c, tg, st)
                     : tbj_levels<T, Ar, true, false, W, H, D>(ctx, g_even, g_odd, f, g, c, tg, st);
   return weighted ? tbj_levels<T, Ar, false, true, W, H, D>(ctx, g_even, g_odd, f, g, c, tg, st)
                   : tbj_levels<T, Ar, false, false, W, H, D>(ctx, g_even, g_odd, f, g, c, tg, st);
+}
+
+// FP64: the z-march's integer-pipe forms -- the adaptive arithmetic by default (3 of 5 additions on the
+// integer pipes for non-negative neighbourhoods, else the multiplication in integer arithmetic), int_adds 3
+// the fixed 3-addition form; int_adds 0..2, 4, 5 every operation on the FP64 pipe.  Same bits either way.
+template <typename T, int W, int H, int D>
+static int tbj_dispatch(stencil_ctx* ctx, T* g_even, T* g_odd, const T* f, const Geom& g, Coef<T> c,
+                        const TileGeom& tg, bool weighted, int int_adds, cudaStream_t st) {
+  if constexpr (sizeof(T) == 8) {
+    if (int_adds < 0 || int_adds == kIntAddsAdaptive)
+      return tbj_arith<T, AdaptJacobi, W, H, D>(ctx, g_even, g_odd, f, g, c, tg, weighted, st);
+    if (int_adds == 3)
+      return tbj_arith<T, ArithF64Mix<0x12u>, W, H, D>(ctx, g_even, g_odd, f, g, c, tg, weighted, st);
+  }
+  return tbj_arith<T, typename DefaultArith<T>::type, W, H, D>(ctx, g_even, g_odd, f, g, c, tg, weighted, st);
 }
 
 template <typename T>
@@ -97,7 +111,7 @@ int tb_jacobi_run(stencil_ctx* ctx, T* u, T* tmp, const T* f, const Geom& g, dou
   if (tx == WW && ty == HH && tz == DD) {                                                 \
     TileGeom tg = make_tile_geom(g, WW, HH, DD, nt, nsweeps);                             \
     if ((rc = ensure_slices(ctx, tg, st)) != STENCIL_OK) return rc;                       \
-    return tbj_dispatch<T, WW, HH, DD>(ctx, g_even, g_odd, f, g, c, tg, weighted, st);    \
+    return tbj_dispatch<T, WW, HH, DD>(ctx, g_even, g_odd, f, g, c, tg, weighted, p->int_adds, st); \
   }
   TBJ_TILE(32, 8, 8)
   TBJ_TILE(32, 16, 8)
