@@ -145,9 +145,12 @@ unsigned long long stencil_kernel_launches(const stencil_ctx* ctx);
  *          additions when every neighbour is non-negative, else the additions
  *          on the FP64 pipe and the multiplication by b in exact integer
  *          arithmetic (Poisson iterates take both signs); -1 = the library
- *          default: 6 on the Jacobi z-march (also in place and batched) and
- *          the Gauss-Seidel column march, 1 on the other Gauss-Seidel paths
- *          (which take 6 as 1).  Same bits whatever the value.
+ *          default: 6 on the Jacobi z-march (also in place and batched), the
+ *          Jacobi skewed-tile tasks (nt > 1; they take 6 or -1 as adaptive,
+ *          3 as the fixed 3-addition form, any other value as all on the
+ *          FP64 pipe) and the Gauss-Seidel column march, 1 on the other
+ *          Gauss-Seidel paths (which take 6 as 1).  Same bits whatever the
+ *          value.
  *  FP64 calls with f != NULL and at least two sweeps compute h^2 f once into
  *  a further grid of workspace when the budget has room for it (Jacobi on the
  *  z-march; Gauss-Seidel on the column march at int_adds 0, 2 or 6; batched
