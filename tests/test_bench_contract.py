@@ -73,3 +73,24 @@ def test_committed_traffic_records_name_existing_sources():
         assert os.path.exists(os.path.join(ROOT, src)), src
         assert len(digest) == 16 and float(value) > 0, ln
 
+
+
+def test_temporal_depth_sweep_launch_parameters():
+    """Each point of the temporal-depth sweep runs a configuration the library supports for it: the FP64
+    headline at nt = 1, the multi-sweep column march with the integer-pipe forms it implements at nt = 2..4
+    (FP64 0, 2 or 6), and the library defaults for FP32 Jacobi and for deeper blocking."""
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    assert bench._nt_cfg("jacobi", 1) == {k: bench.HEADLINE["jacobi"][k] for k in ("tile", "variant", "int_adds")}
+    assert bench._nt_cfg("gs", 1) == {k: bench.HEADLINE["gs"][k] for k in ("tile", "variant", "int_adds")}
+    for nt in (2, 3, 4):
+        cfg = bench._nt_cfg("gs", nt)
+        assert cfg["variant"] == 5 and cfg["int_adds"] in (0, 2, 6)
+        assert bench._nt_cfg("gs_f32", nt)["int_adds"] == -1
+    for name in ("jacobi_f32",):
+        for nt in bench.NT_SWEEP:
+            assert bench._nt_cfg(name, nt) == {"tile": (0, 0, 0), "variant": 0, "int_adds": -1}
+    for name in ("jacobi", "gs", "gs_f32"):
+        for nt in (8, 16):
+            assert bench._nt_cfg(name, nt) == {"tile": (0, 0, 0), "variant": 0, "int_adds": -1}
