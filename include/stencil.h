@@ -433,7 +433,7 @@ int stencil_probe_throughput(stencil_ctx* ctx, size_t copy_bytes, stencil_probe_
  * this entry point exists for callers that cannot call cudaMalloc when they
  * need a residual (an application that owns all device memory through its
  * own allocator, a time-critical loop that must not stall or fragment the
- * heap, code about to be recorded into a CUDA graph).  Same arguments,
+ * heap).  Same arguments,
  * results and reduction order as residual_norm (the same kernels), but no
  * context: the work runs on the calling thread's current CUDA device, and u,
  * f and r_out must be device (or managed) memory of that device; anything

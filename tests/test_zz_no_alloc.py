@@ -2,7 +2,7 @@
 
 residual_norm_noalloc serves callers that cannot allocate device memory when
 they need a residual (they own the device memory through their own allocator,
-must not stall on cudaMalloc, or are about to capture a CUDA graph): it keeps
+or must not stall on cudaMalloc): it keeps
 its reduction scratch in a fixed array inside the library.  This file is
 collected last so that a run stopping at the first failure has already run
 every other test; it passes alone in a fresh process and after the others."""
