@@ -20,6 +20,7 @@
 // the launch boundaries and the idle tail of every level.
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "dataflow.cuh"
@@ -31,7 +32,9 @@ namespace stn {
 
 template <typename T, int KIND, int W, int H, int D>
 __global__ void __launch_bounds__(GS_THREADS) dataflow_kernel(DFRun run, SiteTable tb) {
-  using Ar = typename DefaultArith<T>::type;
+  // FP64 Jacobi tasks: the adaptive integer-pipe arithmetic, as the tile tasks of the level launches
+  using Ar = typename std::conditional<KIND == STENCIL_JACOBI && sizeof(T) == 8, AdaptJacobi,
+                                       typename DefaultArith<T>::type>::type;
   __shared__ long long s_q;
   __shared__ int s_off[GS_MAXLEVELS + 1];
   for (;;) {
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(GS_THREADS) dataflow_kernel(DFRun run, SiteTab
     c.b = (T)d.bco;
     c.hh = (T)d.hh;
     const T* f = (const T*)d.f;
-    if (KIND == STENCIL_GS) {
+    if constexpr (KIND == STENCIL_GS) {
       if (f)
         gs_task_body<T, Ar, true, W, H, D>((T*)d.a, f, d.g, c, tb, d.tg, I, J, K, p, s_off);
       else
