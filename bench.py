@@ -806,7 +806,9 @@ def run_suite_served(args):
     or a solve to 1e-8 capped at 2000 fine-grid sweeps; FP64/FP32 smoothing), 150 GB HBM budget, for a range
     of arrival rates; p50/p99 latency, GLUP/s, admitted/cancelled per rate.  At most --slots requests are on
     the device at once; --grace seconds after the end of the arrival window the requests never admitted are
-    cancelled (counted) and the admitted ones drain.  Host inputs and result buffers are page-locked.  Beside it, the same streams served one request at a time through the plain
+    cancelled (counted) and the admitted ones drain.  Host inputs and result buffers are page-locked.  Solve
+    requests run red-black multigrid V(2,2) cycles in FP64, or with --solve mixed FP32 cycles inside FP64
+    defect correction (in both arms).  Beside it, the same streams served one request at a time through the plain
     single-grid calls (copy in, smooth or multigrid-solve, copy out), first come first served: the per-request
     baseline."""
     import numpy as np
@@ -846,7 +848,9 @@ def run_suite_served(args):
         dt = np.float64 if (r.dtype == "f64" or r.kind == "solve") else np.float32
         return nn, dt
 
-    kinds = {"jacobi": capi.STENCIL_REQ_JACOBI, "gs": capi.STENCIL_REQ_GS, "solve": capi.STENCIL_REQ_SOLVE}
+    mixed = args.solve == "mixed"  # solve requests: FP32 multigrid cycles inside FP64 defect correction
+    kinds = {"jacobi": capi.STENCIL_REQ_JACOBI, "gs": capi.STENCIL_REQ_GS,
+             "solve": capi.STENCIL_REQ_SOLVE_MIXED if mixed else capi.STENCIL_REQ_SOLVE}
     outs = {}
 
     def pct(lat, q):
@@ -933,8 +937,10 @@ def run_suite_served(args):
             h = 1.0 / (nn + 1)
             if r.kind == "solve":
                 cyc = 0
-                rel, cyc, _ = capi.stencil_mg_solve(ctx, u, f, h, capi.STENCIL_GS_RB, nu1=2, nu2=2, ncoarse=args.quantum,
-                                                    rtol=r.rtol, max_cycles=r.sweeps // 4)
+                solve = capi.stencil_solve_mixed_mg if mixed else capi.stencil_mg_solve
+                cap = {"max_outer": r.sweeps // 4} if mixed else {"max_cycles": r.sweeps // 4}
+                rel, cyc, _ = solve(ctx, u, f, h, capi.STENCIL_GS_RB, nu1=2, nu2=2, ncoarse=args.quantum,
+                                    rtol=r.rtol, **cap)
                 lup += 4.0 * cyc * nn ** 3
             else:
                 torch.cuda.synchronize()
@@ -967,7 +973,7 @@ def run_suite_served(args):
     line = {"suite": "served", "metric": "p50/p99 latency and GLUP/s vs arrival rate (continuous batching), beside "
                                          "the same streams served one request at a time",
             "unit": "s", "data": "synthetic", "window_s": window, "slots": args.slots,
-            "sweeps_per_round": args.quantum, "results": out}
+            "sweeps_per_round": args.quantum, "solve": args.solve, "results": out}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1006,6 +1012,8 @@ def main():
                     help="--suite served: seconds after the window before unadmitted requests are cancelled")
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--quantum", type=int, default=50, help="--suite served: sweeps per request and round")
+    ap.add_argument("--solve", choices=["f64", "mixed"], default="f64",
+                    help="--suite served: solve requests as FP64 multigrid or FP32 multigrid in FP64 defect correction")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

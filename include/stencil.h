@@ -340,12 +340,16 @@ int stencil_autotune_batched(stencil_ctx* ctx, int n, const void* const* u, cons
                               * coarsest level) when every extent is odd and >= 3, else lexicographic Gauss-Seidel
                               * sweeps; nsweeps caps the fine-grid sweeps, a cycle counting 4; the residual is
                               * tested after each cycle or round of sweeps */
+#define STENCIL_REQ_SOLVE_MIXED 3 /* the same solve with FP32 multigrid V(2,2) cycles (red-black) inside FP64
+                                   * defect correction (stencil_solve_mixed_mg, one FP32 cycle per outer
+                                   * iteration, the FP64 residual after each) when every extent is odd and
+                                   * >= 3, else as STENCIL_REQ_SOLVE; an outer iteration counts 4 sweeps */
 
 typedef struct stencil_server stencil_server;
 
 typedef struct stencil_request {
   int kind;          /* STENCIL_REQ_* */
-  int dtype;         /* STENCIL_F64 or STENCIL_F32 (solve: F64) */
+  int dtype;         /* STENCIL_F64 or STENCIL_F32 (solves: F64) */
   int64_t dims[3];   /* interior extents, each >= 1 */
   double h;          /* mesh width > 0 */
   int nsweeps;       /* sweeps, or the sweep cap of a solve */

@@ -83,6 +83,7 @@ STENCIL_PENDING = 1
 STENCIL_REQ_JACOBI = 0
 STENCIL_REQ_GS = 1
 STENCIL_REQ_SOLVE = 2
+STENCIL_REQ_SOLVE_MIXED = 3
 
 _P = ctypes.c_void_p
 _D = ctypes.c_double

@@ -219,10 +219,11 @@ static void handoff_finished(stencil_server* s) {
 // --- compute thread: one round over the requests on the device --------------
 //
 // Smoothing requests: up to `quantum` sweeps each, all requests of one
-// (smoother, dtype) class in one batched launch.  Solve requests: up to
-// quantum / 4 multigrid V(2,2) cycles each (red-black Gauss-Seidel smoother;
-// plain lexicographic sweeps when an extent cannot coarsen), the residual
-// tested after every cycle.  Requests
+// (smoother, dtype) class in one batched launch; the finished ones are handed
+// to the copy thread at once.  Solve requests: up to quantum / 4 multigrid
+// V(2,2) cycles each (red-black Gauss-Seidel smoother; FP32 cycles inside
+// FP64 defect correction for the mixed kind; plain lexicographic sweeps when
+// an extent cannot coarsen), the residual tested after every cycle.  Requests
 // that finish are handed to the copy thread.
 static bool compute_round(stencil_server* s) {
   std::vector<Req*> act;
@@ -240,7 +241,7 @@ static bool compute_round(stencil_server* s) {
     const int dtype = cls % 2 == 0 ? STENCIL_F64 : STENCIL_F32;
     std::vector<Req*> grp;
     for (Req* q : act)
-      if (q->r.kind != STENCIL_REQ_SOLVE && q->r.dtype == dtype &&
+      if (q->r.kind < STENCIL_REQ_SOLVE && q->r.dtype == dtype &&
           (q->r.kind == STENCIL_REQ_JACOBI ? STENCIL_JACOBI : STENCIL_GS) == smoother)
         grp.push_back(q);
     if (grp.empty()) continue;
@@ -276,7 +277,7 @@ static bool compute_round(stencil_server* s) {
   smooth_lup = lup;
   handoff_finished(s);  // finished smoothing requests go back before the solve cycles run
   for (Req* q : act) {
-    if (q->r.kind != STENCIL_REQ_SOLVE) continue;
+    if (q->r.kind < STENCIL_REQ_SOLVE) continue;
     const bool odd = q->r.dims[0] % 2 && q->r.dims[1] % 2 && q->r.dims[2] % 2 && q->r.dims[0] >= 3 &&
                      q->r.dims[1] >= 3 && q->r.dims[2] >= 3;
     const int rem = q->r.nsweeps - q->done_sweeps;
@@ -288,7 +289,10 @@ static bool compute_round(stencil_server* s) {
     double rel = -1.0;
     int cyc = 0;
     int rc = STENCIL_OK;
-    if (per > 0)
+    if (per > 0 && levels > 1 && q->r.kind == STENCIL_REQ_SOLVE_MIXED)  // FP32 cycles, FP64 residual and update
+      rc = stencil_solve_mixed_mg(ctx, (double*)q->du, (const double*)q->df, q->r.dims, q->r.h, STENCIL_GS_RB, 2, 2,
+                                  s->quantum, levels, q->r.rtol, maxc, 1, &rel, &cyc, st);
+    else if (per > 0)
       rc = stencil_mg_solve(ctx, (double*)q->du, (const double*)q->df, q->r.dims, q->r.h,
                             levels > 1 ? STENCIL_GS_RB : STENCIL_GS, 2, 2, levels > 1 ? s->quantum : per, levels,
                             q->r.rtol, maxc, &rel, &cyc, st);
@@ -401,9 +405,9 @@ int stencil_server_create(stencil_server** out, int device, size_t hbm_budget_by
 
 int stencil_server_submit(stencil_server* s, const stencil_request* r, uint64_t* ticket) {
   if (!s || !r || !ticket) return STENCIL_ERR_ARG;
-  if (r->kind < STENCIL_REQ_JACOBI || r->kind > STENCIL_REQ_SOLVE) return STENCIL_ERR_ARG;
+  if (r->kind < STENCIL_REQ_JACOBI || r->kind > STENCIL_REQ_SOLVE_MIXED) return STENCIL_ERR_ARG;
   if (r->dtype != STENCIL_F64 && r->dtype != STENCIL_F32) return STENCIL_ERR_ARG;
-  if (r->kind == STENCIL_REQ_SOLVE && (r->dtype != STENCIL_F64 || !(r->rtol > 0.0))) return STENCIL_ERR_ARG;
+  if (r->kind >= STENCIL_REQ_SOLVE && (r->dtype != STENCIL_F64 || !(r->rtol > 0.0))) return STENCIL_ERR_ARG;
   if (!r->u_in || r->nsweeps < 0 || !(r->h > 0.0)) return STENCIL_ERR_ARG;
   for (int d = 0; d < 3; ++d)
     if (r->dims[d] < 1 || r->dims[d] > (1 << 20)) return STENCIL_ERR_ARG;

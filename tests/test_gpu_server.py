@@ -127,6 +127,37 @@ def test_solve_request_runs_multigrid_cycles():
         assert np.array_equal(out2, ref2)
 
 
+def test_mixed_solve_request_runs_fp32_cycles_in_defect_correction():
+    """A mixed-precision solve request on odd extents runs FP32 multigrid V(2,2) cycles inside FP64 defect
+    correction (up to sweeps_per_round / 4 outer iterations per round, the FP64 residual after each): the
+    result equals the oracle's mixed solve with the same stopping test, bit for bit, four sweeps counted per
+    outer iteration; capped before convergence it reports its residual; on even extents it falls back to the
+    plain solve's lexicographic sweeps."""
+    p = W.sine_modes_problem(31, seed=4)
+    u0 = np.zeros_like(p.f)
+    with capi.Server(0, sweeps_per_round=10) as srv:
+        out = np.empty_like(u0)
+        res = srv.wait(srv.submit(capi.STENCIL_REQ_SOLVE_MIXED, u0, p.f, p.h, 400, rtol=1e-8, u_out=out), 120)
+        assert res["status"] == capi.STENCIL_OK and res["rel_residual"] <= 1e-8
+        its = res["sweeps_done"] // 4
+        assert res["sweeps_done"] == 4 * its and 3 <= its <= 15
+        ref, rel, n, ok = oracle.solve_mixed_mg(u0, p.f, p.h, oracle.MG_GS_RB, 2, 2, 10, 32, 1e-8, its, 1)
+        assert ok and n == its
+        assert np.array_equal(out, ref)
+        out2 = np.empty_like(u0)
+        res2 = srv.wait(srv.submit(capi.STENCIL_REQ_SOLVE_MIXED, u0, p.f, p.h, 9, rtol=1e-8, u_out=out2), 60)
+        assert res2["status"] == capi.STENCIL_ERR_NOT_CONVERGED and res2["sweeps_done"] == 8
+        ref2, _, _, _ = oracle.solve_mixed_mg(u0, p.f, p.h, oracle.MG_GS_RB, 2, 2, 10, 32, 1e-8, 2, 1)
+        assert np.array_equal(out2, ref2)
+        # even extents: the same lexicographic sweeps as the plain solve request
+        q = W.random_grid(12, 10, 8, seed=9, with_f=True)
+        out3, out4 = np.empty_like(q[0]), np.empty_like(q[0])
+        r3 = srv.wait(srv.submit(capi.STENCIL_REQ_SOLVE_MIXED, q[0], q[1], 0.1, 25, rtol=1e-12, u_out=out3), 60)
+        r4 = srv.wait(srv.submit(capi.STENCIL_REQ_SOLVE, q[0], q[1], 0.1, 25, rtol=1e-12, u_out=out4), 60)
+        assert r3["status"] == r4["status"] and r3["sweeps_done"] == r4["sweeps_done"]
+        assert np.array_equal(out3, out4)
+
+
 def test_many_requests_overlap_copies_and_rounds():
     """Forty requests of mixed kinds submitted at once through a four-slot server: copies and rounds
     interleave (admission keeps at most four on the device), every result equals the oracle, and the pool
