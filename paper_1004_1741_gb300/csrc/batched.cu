@@ -282,7 +282,8 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
   const size_t bytes = (size_t)g.sy * (size_t)(g.nz + 2) * esz;
   // candidates: (variant, nt, tile, int_adds); the caller's grid is copied, never modified.  int_adds -1 is
   // each path's default (the adaptive form on the z-march and the column march); FP64 also tries the fixed
-  // forms those two are fastest with on non-negative data (3 and 2 integer-pipe additions)
+  // forms those two are fastest with on non-negative data (3 and 2 integer-pipe additions; 3 on the
+  // one-sweep column march with 8x16 columns)
   struct Cand {
     int variant, nt, tx, ty, tz, int_adds;
   };
@@ -295,11 +296,16 @@ int stencil_autotune(stencil_ctx* ctx, int smoother, int dtype, const void* u, c
       for (int ty : {8, 16}) cands.push_back({4, 1, 8, ty, 0, ia});
       cands.push_back({4, 1, 16, 8, 0, ia});
       cands.push_back({5, 1, 0, 0, 0, ia});  // the same as one persistent launch
+      cands.push_back({5, 1, 8, 16, 0, ia});
       for (int nt : {2, 3, 4})                // tasks of nt sweeps in one march
         for (int tx : {8, 16}) {
           cands.push_back({4, nt, tx, 8, 0, ia});
           cands.push_back({5, nt, tx, 8, 0, ia});
         }
+    }
+    if (f64) {
+      cands.push_back({5, 1, 8, 16, 0, 3});
+      cands.push_back({4, 1, 8, 16, 0, 3});
     }
     const int nts[] = {1, 2, 4, 8};
     const int tiles[][3] = {{16, 16, 16}, {32, 8, 8}, {32, 16, 16}};
