@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_int_add_any_kernel(int it
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int c = 0; c < PROBE_CH; ++c) {
+      const double bb = (it & 1) ? b : -b;
       double r;
-      if (!int_add_f64_any(v[c], (it & 1) ? b : -b, &r)) r = ArithF64Fma::add(v[c], b);
+      if (!int_add_f64_any(v[c], bb, &r)) r = ArithF64Fma::add(v[c], bb);
       v[c] = __hiloint2double((__double2hiint(r) & 0x80000000) | 0x3FF00000, __double2loint(r));
     }
   }
