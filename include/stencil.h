@@ -376,7 +376,8 @@ typedef struct stencil_server_stats {
   size_t hbm_in_use, hbm_peak; /* request memory on the device */
   int queue_depth, active;
   double smooth_lup, smooth_s; /* smoothing requests: updates and seconds of their batched launches */
-  double solve_cycles, solve_s; /* solve requests: multigrid cycles (or rounds of sweeps) and their seconds */
+  double solve_cycles, solve_s; /* solve requests: multigrid cycles (mixed: outer iterations; one level: rounds
+                                 * of sweeps) and their seconds */
   double copy_bytes, copy_s;    /* bytes copied in and out by the copy thread and the seconds it spent copying */
 } stencil_server_stats;
 
